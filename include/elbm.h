@@ -1,0 +1,224 @@
+/*
+ * elbm.h -- C ABI of the GB300 (sm_103a) entropic lattice Boltzmann library.
+ *
+ * The library advances a periodic lattice by the ELBM update, Eq. (1) of
+ * Zhao & Yong, "Relaxation-rate formula for the entropic lattice Boltzmann
+ * method":
+ *     f_i(x + c_i, t + 1) = f_i(x, t) + alpha beta (f^eq_i(x, t) - f_i(x, t)),
+ * with beta = c_s^2 / (2 nu + c_s^2) (Eq. (2), dt = 1, c_s^2 = 1/3), f^eq the
+ * minimiser of H(f) = sum_i f_i ln(f_i / W_i) (Eq. (3)) under the mass and
+ * momentum constraints, and alpha chosen per node by
+ *   ELBM_ALPHA_FORMULA: alpha_* = min(2, alpha_max) (Eq. (8)) when
+ *                       H(f*(alpha_*)) <= H(f), else Eq. (9);
+ *   ELBM_ALPHA_ROOT:    the bisection root of H(f + alpha (f^eq - f)) = H(f)
+ *                       (Eq. (4)) on [1, alpha_max], stopped when
+ *                       -1e-13 <= H(f*(alpha)) - H(f) <= 0 (the comparison
+ *                       method of the paper's double-shear-layer experiment);
+ *   ELBM_ALPHA_SECANT:  the modified secant iteration of the paper's
+ *                       conclusion, whose first iterate is Eq. (9).
+ *
+ * Conventions
+ *   - Lattice units: dt = 1, c_s^2 = 1/3.  Periodic boundaries on all axes.
+ *   - Velocity ordering (index: velocity), rest first, then +/- pairs:
+ *       D2Q9:  0 (0,0)  1 (1,0)  2 (-1,0)  3 (0,1)  4 (0,-1)
+ *              5 (1,1)  6 (-1,-1) 7 (1,-1) 8 (-1,1)
+ *       D3Q27: 0 (0,0,0); faces 1 (1,0,0) 2 (-1,0,0) 3 (0,1,0) 4 (0,-1,0)
+ *              5 (0,0,1) 6 (0,0,-1); edges 7 (1,1,0) 8 (-1,-1,0)
+ *              9 (1,-1,0) 10 (-1,1,0) 11 (1,0,1) 12 (-1,0,-1) 13 (1,0,-1)
+ *              14 (-1,0,1) 15 (0,1,1) 16 (0,-1,-1) 17 (0,1,-1) 18 (0,-1,1);
+ *              corners 19 (1,1,1) 20 (-1,-1,-1) 21 (1,1,-1) 22 (-1,-1,1)
+ *              23 (1,-1,1) 24 (-1,1,-1) 25 (-1,1,1) 26 (1,-1,-1)
+ *     Weights are products of the D1Q3 weights {2/3, 1/6, 1/6}.
+ *   - Field layouts (all x fastest): scalar fields [nz][ny][nx]; velocity
+ *     [d][nz][ny][nx] with d = 2 (D2Q9) or 3 (D3Q27); populations
+ *     [Q][nz][ny][nx].  2D lattices use nz = 1.
+ *   - "Step n" state is the pre-collision f^n (left-hand side of Eq. (1) at
+ *     t = n).  Readouts (moments, populations) return f^n.
+ *   - Every host pointer argument is a caller-owned HOST buffer unless the
+ *     name ends in _device; the library copies from/to it and keeps no
+ *     reference.  Device buffers are owned by the handle.
+ *   - Every call returns an elbm_status; no exception or abort crosses the
+ *     ABI.  elbm_step is asynchronous on the handle's stream; the calls that
+ *     return data synchronise that stream and report errors the kernels
+ *     flagged (ELBM_ENEGATIVE for a population <= 0, ELBM_ENONFINITE for a
+ *     NaN/Inf or |u| >= 1); after such an error the state is undefined until
+ *     the next elbm_init_fields / elbm_set_populations.
+ *   - Threading: a handle is used by one host thread at a time.
+ */
+#ifndef ELBM_H
+#define ELBM_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define ELBM_API __attribute__((visibility("default")))
+#else
+#define ELBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct elbm_handle elbm_handle;
+
+typedef enum { ELBM_D2Q9 = 0, ELBM_D3Q27 = 1 } elbm_lattice;
+
+/* Storage (and arithmetic) of the populations.
+ *   ELBM_FP64          f_i in FP64, FP64 arithmetic throughout.
+ *   ELBM_FP32          f_i in FP32.
+ *   ELBM_FP32_SHIFTED  delta_i = f_i - W_i rho0 in FP32 (rho0 a per-handle
+ *                      constant, the FP32-rounded mean initial density).
+ * FP32 storages compute FORMULA in FP32 with a certified error bound on the
+ * entropy differences (see elbm_step); ROOT and SECANT, and nodes far from
+ * equilibrium, are computed in FP64 from the stored values. */
+typedef enum {
+  ELBM_FP64 = 0,
+  ELBM_FP32 = 1,
+  ELBM_FP32_SHIFTED = 2
+} elbm_dtype;
+
+typedef enum {
+  ELBM_ALPHA_FORMULA = 0,
+  ELBM_ALPHA_ROOT = 1,
+  ELBM_ALPHA_SECANT = 2
+} elbm_alpha_mode;
+
+typedef enum {
+  ELBM_OK = 0,
+  ELBM_EINVAL = 1,      /* invalid argument                                */
+  ELBM_ENOMEM = 2,      /* device allocation failed                        */
+  ELBM_ECUDA = 3,       /* CUDA runtime error (message in elbm_last_error) */
+  ELBM_ENONFINITE = 4,  /* a node had NaN/Inf moments or |u_a| >= 1        */
+  ELBM_ENEGATIVE = 5,   /* a node had a population <= 0                    */
+  ELBM_EROOT_CAP = 6,   /* reserved                                        */
+  ELBM_ESTATE = 7       /* call not valid in the handle's state            */
+} elbm_status;
+
+/* Diagnostics of one step (the step that maps f^n to f^{n+1}): moments and
+ * entropy of f^n and counters of the collisions performed. */
+typedef struct {
+  long long step;           /* n                                          */
+  long long n_nodes;
+  double mass;              /* sum_x rho                                  */
+  double momentum[3];       /* sum_x rho u                                */
+  double kinetic_energy;    /* 1/2 sum_x rho |u|^2                        */
+  double alpha_min, alpha_max, alpha_sum;
+  long long n_accept_two;   /* alpha_* = 2 accepted (Fig. 5 counter)      */
+  long long n_accept_star;  /* alpha_* accepted (any alpha_*)             */
+  long long n_formula;      /* Eq. (9) / secant / root alpha used         */
+  long long n_band;         /* FP32 FORMULA: sign of Delta H(2) not
+                               certified, conservative Eq. (9) chord used  */
+  long long n_far;          /* FP32 FORMULA: node solved in FP64 (far from
+                               equilibrium)                               */
+  long long n_degenerate;   /* f^eq == f: alpha = 2                       */
+  long long n_root_iters;   /* ROOT/SECANT iterations                     */
+  long long n_root_cap;     /* ROOT stopped at the iteration cap          */
+  long long n_no_root;      /* ROOT: Delta H(alpha_max) <= 0, alpha_max   */
+  int checked;              /* 1: the FP64 check below was evaluated      */
+  int reserved;
+  double h_total;           /* sum_x H(f^n(x)), Eq. (3), FP64             */
+  long long n_violations;   /* nodes with Delta H(alpha) above its FP64
+                               rounding bound (Eq. (7) violated)          */
+  long long n_decision_mismatch; /* FP32 accept/formula decision differs
+                               from the FP64 one                          */
+  double alpha_dev_max;     /* max |alpha - alpha_FORMULA in FP64|        */
+} elbm_entropy_stats_t;
+
+/* Create a handle for a periodic nx x ny x nz lattice (nz = 1 for D2Q9) of
+ * viscosity nu > 0 (beta from Eq. (2)).  No device memory is touched until
+ * elbm_init_fields / elbm_set_populations.  *out is NULL on failure. */
+ELBM_API elbm_status elbm_create(elbm_handle **out, elbm_lattice lattice, int nx,
+                        int ny, int nz, double nu, elbm_dtype dtype);
+
+/* Destroy a handle and free its device buffers (synchronises its stream). */
+ELBM_API void elbm_destroy(elbm_handle *h);
+
+/* Message of the last failed call on h (or of the last failed elbm_create
+ * when h is NULL).  Valid until the next call on h. */
+ELBM_API const char *elbm_last_error(const elbm_handle *h);
+
+/* Run the handle's work on the given cudaStream_t (NULL: legacy default
+ * stream).  The caller keeps ownership of the stream. */
+ELBM_API elbm_status elbm_set_stream(elbm_handle *h, void *cuda_stream);
+
+/* Device memory callbacks used for every buffer the handle allocates
+ * (NULL alloc: cudaMalloc/cudaFree).  Valid only before the first
+ * allocation (ELBM_ESTATE otherwise). */
+ELBM_API elbm_status elbm_set_allocator(elbm_handle *h,
+                               void *(*alloc)(size_t bytes, void *ctx),
+                               void (*free_fn)(void *ptr, void *ctx),
+                               void *ctx);
+
+/* Diagnostics schedule: fused statistics on steps n with n % diag_every == 0
+ * (0: never), the FP64 entropy/violation check on steps with
+ * n % check_every == 0 (0: never), alpha map written on steps with
+ * n % alpha_map_every == 0 (0: never), and the iteration count of
+ * ELBM_ALPHA_SECANT (>= 1).  Defaults: 1, 0, 0, 4. */
+ELBM_API elbm_status elbm_set_diagnostics(elbm_handle *h, int diag_every,
+                                 int check_every, int alpha_map_every,
+                                 int secant_iters);
+
+/* f^0 = f^eq(rho, u) at every node.  rho: [nz][ny][nx] > 0,
+ * u: [d][nz][ny][nx] with |u_a| < 1, FP64 host buffers.  Resets the step
+ * counter to 0 and sets rho0 to the FP32-rounded mean of rho. */
+ELBM_API elbm_status elbm_init_fields(elbm_handle *h, const double *rho,
+                             const double *u);
+/* Same with device pointers (on the handle's device, FP64). */
+ELBM_API elbm_status elbm_init_fields_device(elbm_handle *h, const double *rho_device,
+                                    const double *u_device);
+
+/* Set the pre-collision state f^n from FP64 populations [Q][nz][ny][nx]
+ * (host), rounded to the storage type.  Resets the step counter to 0. */
+ELBM_API elbm_status elbm_set_populations(elbm_handle *h, const double *f);
+
+/* Advance nsteps >= 0 steps of Eq. (1) with the given alpha mode.
+ * Asynchronous on the handle's stream.
+ * FP32 FORMULA: Delta H(2) and Delta H(1) are evaluated in FP32 from the
+ * moments sum_i f_i x_i^k (k = 2..6) with a bound E on their error; alpha = 2
+ * is accepted only when Delta H(2) + E <= 0, otherwise alpha is the Eq. (9)
+ * chord evaluated on the upper bounds and rounded down, so H(f*(alpha)) <=
+ * H(f) holds for the stored state; nodes with max|x_i| > 1/8 or
+ * alpha_max < 2.5 are solved in FP64. */
+ELBM_API elbm_status elbm_step(elbm_handle *h, long long nsteps, elbm_alpha_mode mode);
+
+/* Block until the handle's queued work is done; reports flagged errors. */
+ELBM_API elbm_status elbm_sync(elbm_handle *h);
+
+/* Density [nz][ny][nx] and velocity [d][nz][ny][nx] of f^n (host, FP64).
+ * Either pointer may be NULL.  Synchronises. */
+ELBM_API elbm_status elbm_moments(elbm_handle *h, double *rho_out, double *u_out);
+
+/* Populations f^n as FP64 [Q][nz][ny][nx] (host).  Synchronises. */
+ELBM_API elbm_status elbm_get_populations(elbm_handle *h, double *f_out);
+
+/* Populations f^n of `count` nodes (flat indices (z ny + y) nx + x), written
+ * as f_out[k * Q + i] (host).  Synchronises. */
+ELBM_API elbm_status elbm_get_populations_nodes(elbm_handle *h, const long long *nodes,
+                                       int count, double *f_out);
+
+/* Per-node alpha [nz][ny][nx] (FP32, host) of the last step that wrote the
+ * alpha map (ELBM_ESTATE if none did).  Synchronises. */
+ELBM_API elbm_status elbm_alpha_map(elbm_handle *h, float *alpha_out);
+
+/* Diagnostics of the last step that computed them (ELBM_ESTATE if none).
+ * Synchronises. */
+ELBM_API elbm_status elbm_entropy_stats(elbm_handle *h, elbm_entropy_stats_t *out);
+
+/* Steps taken since the last initialisation. */
+ELBM_API long long elbm_step_count(const elbm_handle *h);
+
+/* Bytes of device memory held by the handle. */
+ELBM_API size_t elbm_device_bytes(const elbm_handle *h);
+
+/* Number of CUDA kernel launches issued by the library in this process
+ * (all handles).  Used to account the work of a timed region. */
+ELBM_API long long elbm_launch_count(void);
+
+/* Reference density rho0 of the shifted storage (meaningful after init). */
+ELBM_API double elbm_rho0(const elbm_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ELBM_H */

@@ -1,0 +1,32 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "stream_collide.cuh"
+
+namespace elbm {
+
+// Launch counter shared by all launch sites.
+void count_launch();
+
+// Per-translation-unit launchers.  grid <= 0 picks the occupancy-sized grid
+// (SM count x resident blocks, capped by the work); *grid_used receives it.
+#define ELBM_DECLARE_LAUNCHERS(LAT)                                          \
+  cudaError_t launch_fp32_formula_##LAT(int diag, int check,                 \
+                                        const StepParams& p, int grid,        \
+                                        int block, cudaStream_t s,            \
+                                        int* grid_used);                      \
+  cudaError_t launch_far_##LAT(int diag, int check, const StepParams& p,     \
+                               int grid, cudaStream_t s);                    \
+  cudaError_t launch_fp32_fp64mode_##LAT(int mode, int diag, int check,      \
+                                         const StepParams& p, int grid,       \
+                                         int block, cudaStream_t s,           \
+                                         int* grid_used);                     \
+  cudaError_t launch_fp64_##LAT(int mode, int diag, int check,               \
+                                const StepParams& p, int grid, int block,     \
+                                cudaStream_t s, int* grid_used);
+ELBM_DECLARE_LAUNCHERS(d2q9)
+ELBM_DECLARE_LAUNCHERS(d3q27)
+#undef ELBM_DECLARE_LAUNCHERS
+
+}  // namespace elbm

@@ -1,0 +1,72 @@
+// Launch helpers for the stream-collide kernels; each translation unit
+// instantiates the subset it owns so the kernels compile in parallel.
+#pragma once
+#include "internal.h"
+
+namespace elbm {
+
+template <class Kernel>
+static int occupancy_grid(Kernel k, int block, long long threads_needed) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, 0);
+  if (per_sm < 1) per_sm = 1;
+  long long g = (long long)sms * per_sm;
+  const long long need = (threads_needed + block - 1) / block;
+  if (need < g) g = need;
+  return g < 1 ? 1 : (int)g;
+}
+
+template <class L, class T, int MODE, int DIAG, int CHECK>
+static cudaError_t launch_one(const StepParams& p, int grid, int block,
+                              cudaStream_t s, int* grid_used) {
+  auto k = k_stream_collide<L, T, MODE, DIAG, CHECK>;
+  if (grid <= 0) grid = occupancy_grid(k, block, p.tiles * 32);
+  if (grid_used) *grid_used = grid;
+  k<<<grid, block, 0, s>>>(p);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <class L, class T, int MODE>
+static cudaError_t launch_diag(int diag, int check, const StepParams& p,
+                               int grid, int block, cudaStream_t s,
+                               int* grid_used) {
+  if (check) return launch_one<L, T, MODE, 1, 1>(p, grid, block, s, grid_used);
+  if (diag) return launch_one<L, T, MODE, 1, 0>(p, grid, block, s, grid_used);
+  return launch_one<L, T, MODE, 0, 0>(p, grid, block, s, grid_used);
+}
+
+template <class L, class T>
+static cudaError_t launch_fp64_modes(int mode, int diag, int check,
+                                     const StepParams& p, int grid, int block,
+                                     cudaStream_t s, int* grid_used) {
+  if (mode == MODE_ROOT)
+    return launch_diag<L, T, MODE_ROOT>(diag, check, p, grid, block, s,
+                                        grid_used);
+  if (mode == MODE_SECANT)
+    return launch_diag<L, T, MODE_SECANT>(diag, check, p, grid, block, s,
+                                          grid_used);
+  return launch_diag<L, T, MODE_FORMULA>(diag, check, p, grid, block, s,
+                                         grid_used);
+}
+
+// The fixup grid must equal the grid of the FP32 step when DIAG is set (its
+// partials rows follow the step's rows); without DIAG any grid works.
+template <class L>
+static cudaError_t launch_far_lattice(int diag, int check,
+                                      const StepParams& p, int grid,
+                                      cudaStream_t s) {
+  if (grid <= 0) grid = 152;
+  if (check)
+    k_far_fixup<L, 1, 1><<<grid, 256, 0, s>>>(p);
+  else if (diag)
+    k_far_fixup<L, 1, 0><<<grid, 256, 0, s>>>(p);
+  else
+    k_far_fixup<L, 0, 0><<<grid, 256, 0, s>>>(p);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace elbm

@@ -1,0 +1,789 @@
+// Host runtime and C ABI of the ELBM library (declared in include/elbm.h):
+// handle and buffer management, initialisation / readout kernels, the
+// per-step launch sequence and the diagnostics finish kernel.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "../../include/elbm.h"
+#include "internal.h"
+
+namespace elbm {
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// ------------------------------------------------------------------------
+// Initialisation / readout kernels (grid-stride over nodes).
+// ------------------------------------------------------------------------
+
+// Entropic equilibrium in FP64: per-axis factors 1 + d(c), d(0) = -s,
+// d(+-1) = +-3u + 2s, s = 3u^2 / (1 + sqrt(1 + 3u^2)).
+template <class L>
+__device__ __forceinline__ void equilibrium_dev(double rho, const double* u,
+                                                double rho0, double* dev_out,
+                                                double* f_out) {
+  double dp[3], dm[3], d0[3];
+#pragma unroll
+  for (int a = 0; a < L::D; ++a) {
+    const double s = 3.0 * u[a] * u[a] / (1.0 + sqrt(1.0 + 3.0 * u[a] * u[a]));
+    dp[a] = 3.0 * u[a] + 2.0 * s;
+    dm[a] = -3.0 * u[a] + 2.0 * s;
+    d0[a] = -s;
+  }
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    double pm1 = 0.0;   // prod (1 + d) - 1
+#pragma unroll
+    for (int a = 0; a < L::D; ++a) {
+      const int c = L::c(i, a);
+      const double d = c == 1 ? dp[a] : (c == -1 ? dm[a] : d0[a]);
+      pm1 = fma(pm1, d, pm1 + d);
+    }
+    // f^eq_i - W_i rho0 = W_i ((rho - rho0) + rho (P_i - 1))
+    dev_out[i] = L::w(i) * ((rho - rho0) + rho * pm1);
+    f_out[i] = L::w(i) * rho * (1.0 + pm1);
+  }
+}
+
+// Storage value of a population f whose deviation from W_i rho0 is dev.
+template <class T>
+__device__ __forceinline__ T to_storage(double f, double dev, int shifted) {
+  if (sizeof(T) == 8) return (T)f;
+  return shifted ? (T)dev : (T)f;
+}
+
+struct Geo {
+  int nx, ny, nz;
+  long long n;
+  double rho0;
+  int shifted;   // FP32_SHIFTED storage
+};
+
+template <class L>
+__device__ __forceinline__ long long shifted_node(const Geo& g, long long node,
+                                                  int i, int sign) {
+  // node + sign * c_i (periodic)
+  int x = (int)(node % g.nx);
+  int y = (int)((node / g.nx) % g.ny);
+  int z = (int)(node / ((long long)g.nx * g.ny));
+  x += sign * L::c(i, 0);
+  y += sign * L::c(i, 1);
+  z += sign * L::c(i, 2);
+  x = x < 0 ? x + g.nx : (x >= g.nx ? x - g.nx : x);
+  y = y < 0 ? y + g.ny : (y >= g.ny ? y - g.ny : y);
+  z = z < 0 ? z + g.nz : (z >= g.nz ? z - g.nz : z);
+  return ((long long)z * g.ny + y) * g.nx + x;
+}
+
+// f^0 = f^eq(rho, u); stored at x - c_i so that the pull gather of step 0
+// returns it at x.
+template <class L, class T>
+__global__ void k_init_feq(Geo g, const double* __restrict__ rho,
+                           const double* __restrict__ u, void* fv,
+                           unsigned* err) {
+  T* __restrict__ f = static_cast<T*>(fv);
+  for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+       node < g.n; node += (long long)gridDim.x * blockDim.x) {
+    double uu[3] = {0.0, 0.0, 0.0};
+    const double r = rho[node];
+    bool bad = !(r > 0.0) || !isfinite(r);
+#pragma unroll
+    for (int a = 0; a < L::D; ++a) {
+      uu[a] = u[a * g.n + node];
+      bad |= !(fabs(uu[a]) < 1.0);
+    }
+    if (bad) atomicOr(err, NF_BAD_NONFINITE);
+    double dev[L::Q], fe[L::Q];
+    equilibrium_dev<L>(bad ? 1.0 : r, uu, g.rho0, dev, fe);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i)
+      f[i * g.n + shifted_node<L>(g, node, i, -1)] =
+          to_storage<T>(fe[i], dev[i], g.shifted);
+  }
+}
+
+// Pre-collision populations f^n (FP64, [Q][N]) -> pull storage.
+template <class L, class T>
+__global__ void k_set_pop(Geo g, const double* __restrict__ fin, void* fv) {
+  T* __restrict__ f = static_cast<T*>(fv);
+  for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+       node < g.n; node += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      const double v = fin[i * g.n + node];
+      const double s = L::w(i) * g.rho0;
+      f[i * g.n + shifted_node<L>(g, node, i, -1)] =
+          to_storage<T>(v, v - s, g.shifted);
+    }
+  }
+}
+
+template <class L, class T>
+__device__ __forceinline__ double load_pre(const Geo& g, const T* f,
+                                           long long node, int i) {
+  const double v = (double)f[i * g.n + shifted_node<L>(g, node, i, -1)];
+  if (sizeof(T) == 4 && g.shifted) return L::w(i) * g.rho0 + v;
+  return v;
+}
+
+// Storage -> pre-collision populations / moments (gather).
+template <class L, class T>
+__global__ void k_get_pop(Geo g, const void* fv, double* __restrict__ out) {
+  const T* __restrict__ f = static_cast<const T*>(fv);
+  for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+       node < g.n; node += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) out[i * g.n + node] = load_pre<L, T>(g, f, node, i);
+  }
+}
+
+template <class L, class T>
+__global__ void k_get_nodes(Geo g, const void* fv,
+                            const long long* __restrict__ nodes, int count,
+                            double* __restrict__ out) {
+  const T* __restrict__ f = static_cast<const T*>(fv);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count;
+       k += gridDim.x * blockDim.x) {
+    const long long node = nodes[k];
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i)
+      out[(long long)k * L::Q + i] = load_pre<L, T>(g, f, node, i);
+  }
+}
+
+template <class L, class T>
+__global__ void k_moments(Geo g, const void* fv, double* __restrict__ rho_out,
+                          double* __restrict__ u_out) {
+  const T* __restrict__ f = static_cast<const T*>(fv);
+  for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+       node < g.n; node += (long long)gridDim.x * blockDim.x) {
+    double rho = 0.0, j[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      const double v = load_pre<L, T>(g, f, node, i);
+      rho += v;
+#pragma unroll
+      for (int a = 0; a < L::D; ++a) {
+        if (L::c(i, a) == 1) j[a] += v;
+        if (L::c(i, a) == -1) j[a] -= v;
+      }
+    }
+    if (rho_out) rho_out[node] = rho;
+    if (u_out) {
+#pragma unroll
+      for (int a = 0; a < L::D; ++a) u_out[a * g.n + node] = j[a] / rho;
+    }
+  }
+}
+
+// Sum the partial rows of one step in a fixed order.
+__global__ void k_finish(const double* __restrict__ partials, int rows,
+                         double* __restrict__ out) {
+  const int k = blockIdx.x;  // slot
+  __shared__ double sm[256];
+  double v = k < S_NSUM ? 0.0 : (k == S_AMIN ? INFINITY : -INFINITY);
+  if (k == S_ADEV) v = 0.0;
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+    const double x = partials[(long long)r * NSTAT + k];
+    v = k < S_NSUM ? v + x : (k == S_AMIN ? fmin(v, x) : fmax(v, x));
+  }
+  sm[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      const double a = sm[threadIdx.x], b = sm[threadIdx.x + w];
+      sm[threadIdx.x] =
+          k < S_NSUM ? a + b : (k == S_AMIN ? fmin(a, b) : fmax(a, b));
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[k] = sm[0];
+}
+
+}  // namespace elbm
+
+using namespace elbm;
+
+// ------------------------------------------------------------------------
+// Handle
+// ------------------------------------------------------------------------
+struct elbm_handle {
+  elbm_lattice lattice;
+  int nx, ny, nz, q, d;
+  long long n;
+  double nu, beta;
+  elbm_dtype dtype;
+  double rho0 = 1.0;
+  cudaStream_t stream = nullptr;
+  void* (*alloc)(size_t, void*) = nullptr;
+  void (*free_fn)(void*, void*) = nullptr;
+  void* alloc_ctx = nullptr;
+  bool allocated = false;
+  void* f[2] = {nullptr, nullptr};
+  int cur = 0;
+  float* alpha_map = nullptr;
+  bool alpha_map_valid = false;
+  double* partials = nullptr;
+  int partial_rows_max = 0;
+  double* stats_dev = nullptr;
+  unsigned* err_flags = nullptr;
+  unsigned* far_count = nullptr;
+  unsigned* far_queue = nullptr;
+  long long step = 0;
+  int diag_every = 1, check_every = 0, amap_every = 0, secant_iters = 4;
+  bool stats_valid = false;
+  long long stats_step = 0;
+  int stats_checked = 0;
+  size_t bytes = 0;
+  std::vector<std::pair<void*, size_t>> owned;
+  std::string err;
+};
+
+static thread_local std::string g_create_err;
+
+static size_t elem_size(elbm_dtype t) { return t == ELBM_FP64 ? 8 : 4; }
+
+static elbm_status fail(elbm_handle* h, elbm_status st, const std::string& m) {
+  if (h)
+    h->err = m;
+  else
+    g_create_err = m;
+  return st;
+}
+
+static elbm_status cuda_fail(elbm_handle* h, cudaError_t e, const char* what) {
+  return fail(h, ELBM_ECUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static void* dev_alloc(elbm_handle* h, size_t bytes) {
+  void* p = nullptr;
+  if (h->alloc) {
+    p = h->alloc(bytes, h->alloc_ctx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) {
+    h->owned.push_back({p, bytes});
+    h->bytes += bytes;
+  }
+  return p;
+}
+
+static void dev_free(elbm_handle* h, void* p) {
+  if (!p) return;
+  for (size_t k = 0; k < h->owned.size(); ++k) {
+    if (h->owned[k].first == p) {
+      h->bytes -= h->owned[k].second;
+      h->owned.erase(h->owned.begin() + k);
+      break;
+    }
+  }
+  if (h->free_fn)
+    h->free_fn(p, h->alloc_ctx);
+  else
+    cudaFree(p);
+}
+
+static int max_grid_rows() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms * 8;   // at most 8 resident 256-thread blocks per SM
+}
+
+static elbm_status ensure_buffers(elbm_handle* h) {
+  if (h->allocated) return ELBM_OK;
+  const size_t fb = (size_t)h->q * h->n * elem_size(h->dtype);
+  h->f[0] = dev_alloc(h, fb);
+  h->f[1] = dev_alloc(h, fb);
+  h->partial_rows_max = 2 * max_grid_rows();
+  h->partials =
+      (double*)dev_alloc(h, sizeof(double) * NSTAT * h->partial_rows_max);
+  h->stats_dev = (double*)dev_alloc(h, sizeof(double) * NSTAT);
+  h->err_flags = (unsigned*)dev_alloc(h, 256);
+  h->far_count = (unsigned*)dev_alloc(h, 256);
+  if (h->dtype != ELBM_FP64)
+    h->far_queue = (unsigned*)dev_alloc(h, sizeof(unsigned) * h->n);
+  if (!h->f[0] || !h->f[1] || !h->partials || !h->stats_dev ||
+      !h->err_flags || !h->far_count ||
+      (h->dtype != ELBM_FP64 && !h->far_queue))
+    return fail(h, ELBM_ENOMEM, "device allocation failed");
+  cudaMemsetAsync(h->err_flags, 0, 256, h->stream);
+  cudaMemsetAsync(h->far_count, 0, 256, h->stream);
+  h->allocated = true;
+  return ELBM_OK;
+}
+
+static elbm_status ensure_alpha_map(elbm_handle* h) {
+  if (h->alpha_map) return ELBM_OK;
+  h->alpha_map = (float*)dev_alloc(h, sizeof(float) * h->n);
+  if (!h->alpha_map) return fail(h, ELBM_ENOMEM, "alpha map allocation failed");
+  return ELBM_OK;
+}
+
+static Geo geo(const elbm_handle* h) {
+  Geo g;
+  g.nx = h->nx;
+  g.ny = h->ny;
+  g.nz = h->nz;
+  g.n = h->n;
+  g.rho0 = h->dtype == ELBM_FP64 ? 0.0 : h->rho0;
+  g.shifted = h->dtype == ELBM_FP32_SHIFTED;
+  return g;
+}
+
+static int grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  int cap = max_grid_rows();
+  return (int)(g < cap ? (g < 1 ? 1 : g) : cap);
+}
+
+// Dispatch a node-parallel helper kernel on (lattice, storage type).
+#define DISPATCH_LT(h, KERNEL, ...)                                          \
+  do {                                                                       \
+    const int grid_ = grid_for((h)->n);                                      \
+    if ((h)->lattice == ELBM_D2Q9) {                                         \
+      if ((h)->dtype == ELBM_FP64)                                           \
+        KERNEL<D2Q9, double><<<grid_, 256, 0, (h)->stream>>>(__VA_ARGS__);   \
+      else                                                                   \
+        KERNEL<D2Q9, float><<<grid_, 256, 0, (h)->stream>>>(__VA_ARGS__);    \
+    } else {                                                                 \
+      if ((h)->dtype == ELBM_FP64)                                           \
+        KERNEL<D3Q27, double><<<grid_, 256, 0, (h)->stream>>>(__VA_ARGS__);  \
+      else                                                                   \
+        KERNEL<D3Q27, float><<<grid_, 256, 0, (h)->stream>>>(__VA_ARGS__);   \
+    }                                                                        \
+    count_launch();                                                          \
+  } while (0)
+
+static elbm_status check_errors(elbm_handle* h) {
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "stream synchronize");
+  if (!h->allocated) return ELBM_OK;
+  unsigned flags = 0;
+  e = cudaMemcpy(&flags, h->err_flags, sizeof(unsigned),
+                 cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "read error flags");
+  if (flags & NF_BAD_NEG)
+    return fail(h, ELBM_ENEGATIVE, "a node had a population <= 0");
+  if (flags & NF_BAD_NONFINITE)
+    return fail(h, ELBM_ENONFINITE,
+                "a node had non-finite moments or |u| >= 1");
+  return ELBM_OK;
+}
+
+extern "C" {
+
+elbm_status elbm_create(elbm_handle** out, elbm_lattice lattice, int nx,
+                        int ny, int nz, double nu, elbm_dtype dtype) {
+  if (!out) return fail(nullptr, ELBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (lattice != ELBM_D2Q9 && lattice != ELBM_D3Q27)
+    return fail(nullptr, ELBM_EINVAL, "unknown lattice");
+  if (dtype != ELBM_FP64 && dtype != ELBM_FP32 && dtype != ELBM_FP32_SHIFTED)
+    return fail(nullptr, ELBM_EINVAL, "unknown dtype");
+  if (nx < 1 || ny < 1 || nz < 1)
+    return fail(nullptr, ELBM_EINVAL, "lattice dimensions must be >= 1");
+  if (lattice == ELBM_D2Q9 && nz != 1)
+    return fail(nullptr, ELBM_EINVAL, "D2Q9 needs nz == 1");
+  if (!(nu > 0.0) || !(nu < 1e6))
+    return fail(nullptr, ELBM_EINVAL, "nu must be > 0");
+  const long long n = (long long)nx * ny * nz;
+  const int q = lattice == ELBM_D2Q9 ? 9 : 27;
+  if (n > 0xffffffffLL || (long long)q * n > (1LL << 40))
+    return fail(nullptr, ELBM_EINVAL, "lattice too large");
+  elbm_handle* h = new elbm_handle();
+  h->lattice = lattice;
+  h->nx = nx;
+  h->ny = ny;
+  h->nz = nz;
+  h->q = q;
+  h->d = lattice == ELBM_D2Q9 ? 2 : 3;
+  h->n = n;
+  h->nu = nu;
+  const double cs2 = 1.0 / 3.0;
+  h->beta = cs2 / (2.0 * nu + cs2);   // Eq. (2), dt = 1
+  h->dtype = dtype;
+  *out = h;
+  return ELBM_OK;
+}
+
+void elbm_destroy(elbm_handle* h) {
+  if (!h) return;
+  if (!h->owned.empty()) cudaStreamSynchronize(h->stream);
+  while (!h->owned.empty()) dev_free(h, h->owned.back().first);
+  delete h;
+}
+
+const char* elbm_last_error(const elbm_handle* h) {
+  return h ? h->err.c_str() : g_create_err.c_str();
+}
+
+elbm_status elbm_set_stream(elbm_handle* h, void* s) {
+  if (!h) return ELBM_EINVAL;
+  h->stream = (cudaStream_t)s;
+  return ELBM_OK;
+}
+
+elbm_status elbm_set_allocator(elbm_handle* h, void* (*alloc)(size_t, void*),
+                               void (*free_fn)(void*, void*), void* ctx) {
+  if (!h) return ELBM_EINVAL;
+  if (h->allocated || !h->owned.empty())
+    return fail(h, ELBM_ESTATE, "allocator must be set before allocation");
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail(h, ELBM_EINVAL, "alloc and free must both be set or NULL");
+  h->alloc = alloc;
+  h->free_fn = free_fn;
+  h->alloc_ctx = ctx;
+  return ELBM_OK;
+}
+
+elbm_status elbm_set_diagnostics(elbm_handle* h, int diag_every,
+                                 int check_every, int alpha_map_every,
+                                 int secant_iters) {
+  if (!h) return ELBM_EINVAL;
+  if (diag_every < 0 || check_every < 0 || alpha_map_every < 0 ||
+      secant_iters < 1 || secant_iters > 1000)
+    return fail(h, ELBM_EINVAL, "invalid diagnostics schedule");
+  h->diag_every = diag_every;
+  h->check_every = check_every;
+  h->amap_every = alpha_map_every;
+  h->secant_iters = secant_iters;
+  return ELBM_OK;
+}
+
+static elbm_status init_common(elbm_handle* h, const double* rho_dev,
+                               const double* u_dev, double rho_mean) {
+  h->rho0 = (double)(float)rho_mean;
+  elbm_status st = ensure_buffers(h);
+  if (st) return st;
+  cudaMemsetAsync(h->err_flags, 0, 256, h->stream);
+  cudaMemsetAsync(h->far_count, 0, 256, h->stream);
+  h->cur = 0;
+  Geo g = geo(h);
+  DISPATCH_LT(h, k_init_feq, g, rho_dev, u_dev, h->f[0], h->err_flags);
+  h->step = 0;
+  h->stats_valid = false;
+  h->alpha_map_valid = false;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "init kernel");
+  return ELBM_OK;
+}
+
+elbm_status elbm_init_fields(elbm_handle* h, const double* rho,
+                             const double* u) {
+  if (!h || !rho || !u) return h ? fail(h, ELBM_EINVAL, "NULL field") : ELBM_EINVAL;
+  double sum = 0.0;
+  for (long long k = 0; k < h->n; ++k) {
+    if (!(rho[k] > 0.0)) return fail(h, ELBM_EINVAL, "rho must be > 0");
+    sum += rho[k];
+  }
+  for (long long k = 0; k < (long long)h->d * h->n; ++k)
+    if (!(u[k] > -1.0 && u[k] < 1.0))
+      return fail(h, ELBM_EINVAL, "|u| must be < 1");
+  elbm_status st = ensure_buffers(h);
+  if (st) return st;
+  const size_t bytes = sizeof(double) * (1 + h->d) * h->n;
+  double* tmp = (double*)dev_alloc(h, bytes);
+  if (!tmp) return fail(h, ELBM_ENOMEM, "staging allocation failed");
+  cudaError_t e = cudaMemcpyAsync(tmp, rho, sizeof(double) * h->n,
+                                  cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(tmp + h->n, u, sizeof(double) * h->d * h->n,
+                        cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) {
+    dev_free(h, tmp);
+    return cuda_fail(h, e, "copy fields");
+  }
+  st = init_common(h, tmp, tmp + h->n, sum / (double)h->n);
+  cudaStreamSynchronize(h->stream);
+  dev_free(h, tmp);
+  if (st) return st;
+  return check_errors(h);
+}
+
+elbm_status elbm_init_fields_device(elbm_handle* h, const double* rho_device,
+                                    const double* u_device) {
+  if (!h || !rho_device || !u_device) return h ? fail(h, ELBM_EINVAL, "NULL field") : ELBM_EINVAL;
+  // rho0 from a strided host sample of the density (rounded to FP32 anyway)
+  const long long stride = h->n > 4096 ? h->n / 4096 : 1;
+  std::vector<double> sample;
+  for (long long k = 0; k < h->n; k += stride) {
+    double v = 0.0;
+    cudaMemcpy(&v, rho_device + k, sizeof(double), cudaMemcpyDeviceToHost);
+    sample.push_back(v);
+  }
+  double sum = 0.0;
+  for (double v : sample) sum += v;
+  elbm_status st = init_common(h, rho_device, u_device,
+                               sum / (double)sample.size());
+  if (st) return st;
+  return check_errors(h);
+}
+
+elbm_status elbm_set_populations(elbm_handle* h, const double* f) {
+  if (!h || !f) return h ? fail(h, ELBM_EINVAL, "NULL populations") : ELBM_EINVAL;
+  double mass = 0.0;
+  for (long long k = 0; k < (long long)h->q * h->n; ++k) {
+    if (!(f[k] > 0.0)) return fail(h, ELBM_EINVAL, "populations must be > 0");
+    mass += f[k];
+  }
+  h->rho0 = (double)(float)(mass / (double)h->n);
+  elbm_status st = ensure_buffers(h);
+  if (st) return st;
+  const size_t bytes = sizeof(double) * h->q * h->n;
+  double* tmp = (double*)dev_alloc(h, bytes);
+  if (!tmp) return fail(h, ELBM_ENOMEM, "staging allocation failed");
+  cudaError_t e =
+      cudaMemcpyAsync(tmp, f, bytes, cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) {
+    dev_free(h, tmp);
+    return cuda_fail(h, e, "copy populations");
+  }
+  cudaMemsetAsync(h->err_flags, 0, 256, h->stream);
+  cudaMemsetAsync(h->far_count, 0, 256, h->stream);
+  h->cur = 0;
+  Geo g = geo(h);
+  DISPATCH_LT(h, k_set_pop, g, (const double*)tmp, h->f[0]);
+  cudaStreamSynchronize(h->stream);
+  dev_free(h, tmp);
+  h->step = 0;
+  h->stats_valid = false;
+  h->alpha_map_valid = false;
+  return check_errors(h);
+}
+
+elbm_status elbm_step(elbm_handle* h, long long nsteps, elbm_alpha_mode mode) {
+  if (!h) return ELBM_EINVAL;
+  if (nsteps < 0) return fail(h, ELBM_EINVAL, "nsteps must be >= 0");
+  if (mode != ELBM_ALPHA_FORMULA && mode != ELBM_ALPHA_ROOT &&
+      mode != ELBM_ALPHA_SECANT)
+    return fail(h, ELBM_EINVAL, "unknown alpha mode");
+  if (!h->allocated)
+    return fail(h, ELBM_ESTATE, "fields not initialised");
+  if (h->amap_every > 0) {
+    elbm_status st = ensure_alpha_map(h);
+    if (st) return st;
+  }
+  StepParams p;
+  memset(&p, 0, sizeof(p));
+  p.nx = h->nx;
+  p.ny = h->ny;
+  p.nz = h->nz;
+  p.n = h->n;
+  p.chunks = (h->nx + 31) / 32;
+  p.tiles = (long long)p.chunks * h->ny * h->nz;
+  p.beta = h->beta;
+  p.rho0 = h->dtype == ELBM_FP64 ? 0.0 : h->rho0;
+  p.unshifted = h->dtype == ELBM_FP32;
+  if (p.unshifted) {
+    const float r0 = (float)h->rho0;
+    double ssum = 0.0;
+    for (int i = 0; i < h->q; ++i) {
+      const double w = h->lattice == ELBM_D2Q9 ? D2Q9::w(i) : D3Q27::w(i);
+      const float s = (float)w * r0;
+      ssum += (double)s;
+      p.corr[i] = (float)(w * h->rho0 - (double)s);
+    }
+    p.corr_rho = (float)(ssum - h->rho0);
+  }
+  p.secant_iters = h->secant_iters;
+  p.partials = h->partials;
+  p.err_flags = h->err_flags;
+  p.far_count = h->far_count;
+  p.far_queue = h->far_queue;
+  const bool d2 = h->lattice == ELBM_D2Q9;
+  const int storage = h->dtype == ELBM_FP64 ? 0 : 1;
+  for (long long s = 0; s < nsteps; ++s) {
+    const long long n = h->step;
+    const int check = h->check_every > 0 && n % h->check_every == 0;
+    const int diag = check || (h->diag_every > 0 && n % h->diag_every == 0);
+    const bool amap = h->amap_every > 0 && n % h->amap_every == 0;
+    p.f_in = h->f[h->cur];
+    p.f_out = h->f[h->cur ^ 1];
+    p.alpha_map = amap ? h->alpha_map : nullptr;
+    p.parity = (int)(n & 1);
+    int grid = 0;
+    cudaError_t e;
+    const bool fp32_formula = storage == 1 && mode == ELBM_ALPHA_FORMULA;
+    if (storage == 0)
+      e = d2 ? launch_fp64_d2q9(mode, diag, check, p, 0, 256, h->stream, &grid)
+             : launch_fp64_d3q27(mode, diag, check, p, 0, 256, h->stream, &grid);
+    else if (fp32_formula)
+      e = d2 ? launch_fp32_formula_d2q9(diag, check, p, 0, 256, h->stream, &grid)
+             : launch_fp32_formula_d3q27(diag, check, p, 0, 256, h->stream,
+                                         &grid);
+    else
+      e = d2 ? launch_fp32_fp64mode_d2q9(mode, diag, check, p, 0, 256,
+                                         h->stream, &grid)
+             : launch_fp32_fp64mode_d3q27(mode, diag, check, p, 0, 256,
+                                          h->stream, &grid);
+    if (e != cudaSuccess) return cuda_fail(h, e, "stream-collide launch");
+    int rows = grid;
+    if (fp32_formula) {
+      StepParams pf = p;
+      pf.partials = h->partials + (size_t)grid * NSTAT;
+      const int fgrid = grid < 152 ? grid : 152;
+      e = d2 ? launch_far_d2q9(diag, check, pf, fgrid, h->stream)
+             : launch_far_d3q27(diag, check, pf, fgrid, h->stream);
+      if (e != cudaSuccess) return cuda_fail(h, e, "far fixup launch");
+      rows += fgrid;
+    }
+    if (diag) {
+      k_finish<<<NSTAT, 256, 0, h->stream>>>(h->partials, rows, h->stats_dev);
+      count_launch();
+      h->stats_valid = true;
+      h->stats_step = n;
+      h->stats_checked = check;
+    }
+    if (amap) h->alpha_map_valid = true;
+    h->cur ^= 1;
+    h->step += 1;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "step");
+  return ELBM_OK;
+}
+
+elbm_status elbm_sync(elbm_handle* h) {
+  if (!h) return ELBM_EINVAL;
+  return check_errors(h);
+}
+
+elbm_status elbm_moments(elbm_handle* h, double* rho_out, double* u_out) {
+  if (!h) return ELBM_EINVAL;
+  if (!h->allocated) return fail(h, ELBM_ESTATE, "fields not initialised");
+  elbm_status st = check_errors(h);
+  if (st) return st;
+  const size_t bytes = sizeof(double) * (1 + h->d) * h->n;
+  double* tmp = (double*)dev_alloc(h, bytes);
+  if (!tmp) return fail(h, ELBM_ENOMEM, "staging allocation failed");
+  Geo g = geo(h);
+  DISPATCH_LT(h, k_moments, g, h->f[h->cur], tmp, tmp + h->n);
+  cudaError_t e = cudaSuccess;
+  if (rho_out)
+    e = cudaMemcpyAsync(rho_out, tmp, sizeof(double) * h->n,
+                        cudaMemcpyDeviceToHost, h->stream);
+  if (u_out && e == cudaSuccess)
+    e = cudaMemcpyAsync(u_out, tmp + h->n, sizeof(double) * h->d * h->n,
+                        cudaMemcpyDeviceToHost, h->stream);
+  cudaError_t e2 = cudaStreamSynchronize(h->stream);
+  dev_free(h, tmp);
+  if (e != cudaSuccess) return cuda_fail(h, e, "copy moments");
+  if (e2 != cudaSuccess) return cuda_fail(h, e2, "moments");
+  return ELBM_OK;
+}
+
+elbm_status elbm_get_populations(elbm_handle* h, double* f_out) {
+  if (!h || !f_out) return h ? fail(h, ELBM_EINVAL, "NULL output") : ELBM_EINVAL;
+  if (!h->allocated) return fail(h, ELBM_ESTATE, "fields not initialised");
+  elbm_status st = check_errors(h);
+  if (st) return st;
+  const size_t bytes = sizeof(double) * h->q * h->n;
+  double* tmp = (double*)dev_alloc(h, bytes);
+  if (!tmp) return fail(h, ELBM_ENOMEM, "staging allocation failed");
+  Geo g = geo(h);
+  DISPATCH_LT(h, k_get_pop, g, h->f[h->cur], tmp);
+  cudaError_t e =
+      cudaMemcpyAsync(f_out, tmp, bytes, cudaMemcpyDeviceToHost, h->stream);
+  cudaError_t e2 = cudaStreamSynchronize(h->stream);
+  dev_free(h, tmp);
+  if (e != cudaSuccess) return cuda_fail(h, e, "copy populations");
+  if (e2 != cudaSuccess) return cuda_fail(h, e2, "populations");
+  return ELBM_OK;
+}
+
+elbm_status elbm_get_populations_nodes(elbm_handle* h, const long long* nodes,
+                                       int count, double* f_out) {
+  if (!h || (count > 0 && (!nodes || !f_out)) || count < 0)
+    return h ? fail(h, ELBM_EINVAL, "invalid node list") : ELBM_EINVAL;
+  if (!h->allocated) return fail(h, ELBM_ESTATE, "fields not initialised");
+  for (int k = 0; k < count; ++k)
+    if (nodes[k] < 0 || nodes[k] >= h->n)
+      return fail(h, ELBM_EINVAL, "node index out of range");
+  elbm_status st = check_errors(h);
+  if (st || count == 0) return st;
+  const size_t ib = sizeof(long long) * count;
+  const size_t ob = sizeof(double) * h->q * count;
+  char* tmp = (char*)dev_alloc(h, ib + ob);
+  if (!tmp) return fail(h, ELBM_ENOMEM, "staging allocation failed");
+  cudaMemcpyAsync(tmp, nodes, ib, cudaMemcpyHostToDevice, h->stream);
+  Geo g = geo(h);
+  const long long* dn = (const long long*)tmp;
+  double* dout = (double*)(tmp + ib);
+  DISPATCH_LT(h, k_get_nodes, g, (const void*)h->f[h->cur], dn, count, dout);
+  cudaError_t e =
+      cudaMemcpyAsync(f_out, dout, ob, cudaMemcpyDeviceToHost, h->stream);
+  cudaError_t e2 = cudaStreamSynchronize(h->stream);
+  dev_free(h, tmp);
+  if (e != cudaSuccess) return cuda_fail(h, e, "copy node populations");
+  if (e2 != cudaSuccess) return cuda_fail(h, e2, "node populations");
+  return ELBM_OK;
+}
+
+elbm_status elbm_alpha_map(elbm_handle* h, float* alpha_out) {
+  if (!h || !alpha_out) return h ? fail(h, ELBM_EINVAL, "NULL output") : ELBM_EINVAL;
+  if (!h->alpha_map_valid)
+    return fail(h, ELBM_ESTATE, "no step has written the alpha map");
+  elbm_status st = check_errors(h);
+  if (st) return st;
+  cudaError_t e = cudaMemcpy(alpha_out, h->alpha_map, sizeof(float) * h->n,
+                             cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "copy alpha map");
+  return ELBM_OK;
+}
+
+elbm_status elbm_entropy_stats(elbm_handle* h, elbm_entropy_stats_t* out) {
+  if (!h || !out) return h ? fail(h, ELBM_EINVAL, "NULL output") : ELBM_EINVAL;
+  if (!h->stats_valid)
+    return fail(h, ELBM_ESTATE, "no step has computed diagnostics");
+  elbm_status st = check_errors(h);
+  if (st) return st;
+  double s[NSTAT];
+  cudaError_t e = cudaMemcpy(s, h->stats_dev, sizeof(s), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "copy stats");
+  memset(out, 0, sizeof(*out));
+  const double rho0 = h->dtype == ELBM_FP64 ? 0.0 : h->rho0;
+  out->step = h->stats_step;
+  out->n_nodes = (long long)s[S_NODES];
+  out->mass = s[S_DRHO] + rho0 * (double)h->n;
+  out->momentum[0] = s[S_J0];
+  out->momentum[1] = s[S_J1];
+  out->momentum[2] = s[S_J2];
+  out->kinetic_energy = s[S_KE];
+  out->alpha_min = s[S_AMIN];
+  out->alpha_max = s[S_AMAX];
+  out->alpha_sum = s[S_ASUM];
+  out->n_accept_two = (long long)s[S_ACC2];
+  out->n_accept_star = (long long)s[S_ACCSTAR];
+  out->n_formula = (long long)s[S_FORMULA];
+  out->n_band = (long long)s[S_BAND];
+  out->n_far = (long long)s[S_FAR];
+  out->n_degenerate = (long long)s[S_DEGEN];
+  out->n_root_iters = (long long)s[S_ITERS];
+  out->n_root_cap = (long long)s[S_CAP];
+  out->n_no_root = (long long)s[S_NOROOT];
+  out->checked = h->stats_checked;
+  out->h_total = s[S_H];
+  out->n_violations = (long long)s[S_VIOL];
+  out->n_decision_mismatch = (long long)s[S_MISMATCH];
+  out->alpha_dev_max = s[S_ADEV];
+  return ELBM_OK;
+}
+
+long long elbm_step_count(const elbm_handle* h) { return h ? h->step : -1; }
+
+size_t elbm_device_bytes(const elbm_handle* h) { return h ? h->bytes : 0; }
+
+long long elbm_launch_count(void) { return g_launches.load(); }
+
+double elbm_rho0(const elbm_handle* h) { return h ? h->rho0 : 0.0; }
+
+}  // extern "C"

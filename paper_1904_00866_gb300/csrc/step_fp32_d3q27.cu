@@ -1,0 +1,15 @@
+// D3Q27: FP32-storage certified FORMULA kernels and the FP64 far-node fixup.
+#include "launch_step.cuh"
+
+namespace elbm {
+cudaError_t launch_fp32_formula_d3q27(int diag, int check, const StepParams& p,
+                                      int grid, int block, cudaStream_t s,
+                                      int* grid_used) {
+  return launch_diag<D3Q27, float, MODE_FORMULA>(diag, check, p, grid, block, s,
+                                                  grid_used);
+}
+cudaError_t launch_far_d3q27(int diag, int check, const StepParams& p, int grid,
+                             cudaStream_t s) {
+  return launch_far_lattice<D3Q27>(diag, check, p, grid, s);
+}
+}  // namespace elbm

@@ -1,0 +1,11 @@
+// D2Q9: FP64-storage kernels (FP64 arithmetic, all alpha modes).
+#include "launch_step.cuh"
+
+namespace elbm {
+cudaError_t launch_fp64_d2q9(int mode, int diag, int check, const StepParams& p,
+                              int grid, int block, cudaStream_t s,
+                              int* grid_used) {
+  return launch_fp64_modes<D2Q9, double>(mode, diag, check, p, grid, block, s,
+                                          grid_used);
+}
+}  // namespace elbm

@@ -1,0 +1,255 @@
+// Fused pull-scheme stream + collide kernel (Eq. (5b) gather, Eq. (5a)
+// relax) for one periodic lattice.
+//
+// Storage: SoA populations [Q][nz][ny][nx], x fastest.  The buffer holds the
+// post-collision values f~ of the previous step; the pre-collision state at
+// node x is the gather f_i(x) = f~_i(x - c_i), so each population array is
+// read once and written once per step (HBM traffic 2 Q sizeof(T) per node).
+//
+// Work decomposition: a tile is 32 consecutive x-nodes of one (y, z) row,
+// one warp per tile; warps stride over tiles (grid sized to the SM count).
+// The 27 (or 9) gathers of a tile are warp-coalesced 128-byte rows; the
+// +-1 x-shift of a row is absorbed by L1/L2.
+//
+// Template parameters: lattice L, storage type T (double: FP64 arithmetic;
+// float: FP32 storage, certified FP32 FORMULA or FP64 ROOT/SECANT), alpha
+// MODE, DIAG (fused statistics), CHECK (FP64 entropy check; implies DIAG).
+#pragma once
+#include <stdint.h>
+
+#include "lattice.cuh"
+#include "node_fp32.cuh"
+#include "node_fp64.cuh"
+#include "stats.cuh"
+
+namespace elbm {
+
+struct StepParams {
+  const void* f_in;
+  void* f_out;
+  float* alpha_map;       // nullptr: not written this step
+  double* partials;       // [gridDim.x][NSTAT] when DIAG
+  unsigned* err_flags;    // OR of NF_BAD_* over the lattice
+  int nx, ny, nz;
+  int chunks;             // ceil(nx / 32)
+  long long n;            // nodes
+  long long tiles;        // chunks * ny * nz
+  double beta;
+  double rho0;            // shift reference (0 for FP64 storage)
+  int unshifted;          // FP32 storage of f itself (not f - W rho0)
+  float corr_rho;         // unshifted: sum_i fl(W_i rho0) - rho0
+  float corr[27];         // unshifted: W_i rho0 - fl(W_i rho0)
+  int secant_iters;
+  unsigned* far_count;    // [2] deferred-node counters, indexed by parity
+  unsigned* far_queue;    // node indices deferred to the FP64 fixup
+  int parity;             // step parity selecting far_count[parity]
+};
+
+template <class L>
+__device__ __forceinline__ void tile_coords(const StepParams& p, long long t,
+                                            int lane, int& x, int& y, int& z) {
+  const long long row = t / p.chunks;
+  const int chunk = (int)(t - row * p.chunks);
+  x = chunk * 32 + lane;
+  y = (int)(row % p.ny);
+  z = (int)(row / p.ny);
+}
+
+// Flat index of the pull source x - c_i of population i.
+template <class L>
+__device__ __forceinline__ long long src_index(const StepParams& p, int i,
+                                               int x, int y, int z) {
+  const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+  int xs = x - cx, ys = y - cy, zs = z - cz;
+  xs = xs < 0 ? xs + p.nx : (xs >= p.nx ? xs - p.nx : xs);
+  ys = ys < 0 ? ys + p.ny : (ys >= p.ny ? ys - p.ny : ys);
+  zs = zs < 0 ? zs + p.nz : (zs >= p.nz ? zs - p.nz : zs);
+  return ((long long)zs * p.ny + ys) * p.nx + xs;
+}
+
+// FP64 collision of one node from FP64 populations f64; writes the new
+// populations through `store(i, value)`.
+template <class L, int MODE, int CHECK, class Store>
+__device__ __forceinline__ void collide64(Node64<L>& nd, const StepParams& p,
+                                          bool round_alpha_down, Acc& acc,
+                                          bool diag, Store store) {
+  unsigned flags = node64_prepare(nd);
+  int iters = 0;
+  double alpha = 2.0;
+  if (flags) {
+    atomicOr(p.err_flags, flags);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) store(i, nd.f[i]);
+    return;
+  }
+  alpha = node64_alpha<L, MODE>(nd, p.secant_iters, flags, iters);
+  if (round_alpha_down) alpha = (double)__double2float_rd(alpha);
+  const double ab = alpha * p.beta;
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) store(i, fma(ab, nd.f[i] * nd.x[i], nd.f[i]));
+  if (diag) {
+    acc.add_moments(nd.rho - p.rho0, nd.j, nd.rho);
+    acc.add_alpha(alpha, flags, iters);
+    if (CHECK) {
+      Check64 ck = node64_check(nd, alpha);
+      acc.add_check(ck.h, ck.violation,
+                    ((flags & NF_ACCEPT_STAR) != 0) != ck.accept_ref,
+                    fabs(alpha - ck.alpha_ref));
+    }
+  }
+  if (p.alpha_map) store(-1, alpha);
+}
+
+template <class L, class T, int MODE, int DIAG, int CHECK>
+__global__ void __launch_bounds__(256)
+    k_stream_collide(const StepParams p) {
+  constexpr int Q = L::Q;
+  const int lane = threadIdx.x & 31;
+  const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const T* __restrict__ fin = static_cast<const T*>(p.f_in);
+  T* __restrict__ fout = static_cast<T*>(p.f_out);
+  Acc acc;
+  acc.init();
+
+  for (long long t = warp0; t < p.tiles; t += nwarps) {
+    int x, y, z;
+    tile_coords<L>(p, t, lane, x, y, z);
+    if (x >= p.nx) continue;
+    const long long node = ((long long)z * p.ny + y) * p.nx + x;
+
+    T v[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) v[i] = fin[(long long)i * p.n + src_index<L>(p, i, x, y, z)];
+
+    auto store_T = [&](int i, double val) {
+      if (i < 0) {
+        p.alpha_map[node] = (float)val;
+      } else {
+        fout[(long long)i * p.n + node] = (T)val;
+      }
+    };
+
+    if constexpr (sizeof(T) == 8) {
+      // ---------------- FP64 storage: FP64 arithmetic -------------------
+      Node64<L> nd;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) nd.f[i] = (double)v[i];
+      collide64<L, MODE, CHECK>(nd, p, false, acc, DIAG != 0, store_T);
+    } else if constexpr (MODE != MODE_FORMULA) {
+      // ------------- FP32 storage, ROOT / SECANT in FP64 -----------------
+      Node64<L> nd;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const double s = L::w(i) * p.rho0;
+        nd.f[i] = p.unshifted ? (double)v[i] : s + (double)v[i];
+      }
+      auto store_s = [&](int i, double val) {
+        if (i < 0) {
+          p.alpha_map[node] = (float)val;
+        } else {
+          const double s = L::w(i) * p.rho0;
+          fout[(long long)i * p.n + node] =
+              (T)(p.unshifted ? val : val - s);
+        }
+      };
+      collide64<L, MODE, CHECK>(nd, p, true, acc, DIAG != 0, store_s);
+    } else {
+      // ------------- FP32 storage, certified FP32 FORMULA ----------------
+      float dl[Q], nn[Q];
+      const float rho0f = (float)p.rho0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        dl[i] = p.unshifted ? (float)v[i] - (float)L::w(i) * rho0f
+                            : (float)v[i];
+      }
+      // (float)W * rho0f is the shift s_i used by the unshifted storage
+      Node32Result r = node32_formula<L>(dl, nn, rho0f,
+                                         p.unshifted ? p.corr_rho : 0.0f,
+                                         p.unshifted ? p.corr : nullptr);
+      if (r.flags & (NF_FAR | NF_BAD_NEG | NF_BAD_NONFINITE)) {
+        if (r.flags & (NF_BAD_NEG | NF_BAD_NONFINITE)) {
+          // invalid state: flag it and pass the loaded values through
+          atomicOr(p.err_flags, r.flags & (NF_BAD_NEG | NF_BAD_NONFINITE));
+#pragma unroll
+          for (int i = 0; i < Q; ++i)
+            fout[(long long)i * p.n + node] =
+                fin[(long long)i * p.n + src_index<L>(p, i, x, y, z)];
+          continue;
+        }
+        // far from equilibrium: the FP64 fixup kernel collides this node
+        // (it re-gathers from f_in, which this step does not modify)
+        const unsigned slot = atomicAdd(&p.far_count[p.parity], 1u);
+        p.far_queue[slot] = (unsigned)node;
+        continue;
+      }
+      const float ab = r.alpha * (float)p.beta;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const float nv = fmaf(ab, nn[i], dl[i]);
+        fout[(long long)i * p.n + node] =
+            p.unshifted ? (T)(nv + (float)L::w(i) * rho0f) : (T)nv;
+      }
+      if (p.alpha_map) p.alpha_map[node] = r.alpha;
+      if (DIAG) {
+        double jd[3] = {r.j[0], r.j[1], r.j[2]};
+        acc.add_moments(r.drho, jd, r.rho);
+        acc.add_alpha(r.alpha, r.flags, 0);
+        if (CHECK) {
+          Node64<L> nd;
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            const double s = L::w(i) * p.rho0;
+            nd.f[i] = p.unshifted ? (double)v[i] : s + (double)v[i];
+          }
+          node64_prepare(nd);
+          Check64 ck = node64_check(nd, (double)r.alpha);
+          acc.add_check(ck.h, ck.violation,
+                        ((r.flags & NF_ACCEPT_STAR) != 0) != ck.accept_ref,
+                        fabs((double)r.alpha - ck.alpha_ref));
+        }
+      }
+    }
+  }
+  if (DIAG) acc.block_reduce_store(p.partials);
+}
+
+// FP64 collision of the nodes the FP32 FORMULA kernel deferred.  Resets
+// the other parity's counter for the next step (stream order makes that
+// counter idle here).
+template <class L, int DIAG, int CHECK>
+__global__ void __launch_bounds__(256) k_far_fixup(const StepParams p) {
+  constexpr int Q = L::Q;
+  const float* __restrict__ fin = static_cast<const float*>(p.f_in);
+  float* __restrict__ fout = static_cast<float*>(p.f_out);
+  const unsigned count = p.far_count[p.parity];
+  Acc acc;
+  acc.init();
+  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < count;
+       k += gridDim.x * blockDim.x) {
+    const long long node = p.far_queue[k];
+    const int x = (int)(node % p.nx);
+    const int y = (int)((node / p.nx) % p.ny);
+    const int z = (int)(node / ((long long)p.nx * p.ny));
+    Node64<L> nd;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const double v = (double)fin[(long long)i * p.n + src_index<L>(p, i, x, y, z)];
+      nd.f[i] = p.unshifted ? v : L::w(i) * p.rho0 + v;
+    }
+    auto store_s = [&](int i, double val) {
+      if (i < 0) {
+        p.alpha_map[node] = (float)val;
+      } else {
+        fout[(long long)i * p.n + node] =
+            (float)(p.unshifted ? val : val - L::w(i) * p.rho0);
+      }
+    };
+    if (DIAG) acc.far += 1;
+    collide64<L, MODE_FORMULA, CHECK>(nd, p, true, acc, DIAG != 0, store_s);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) p.far_count[p.parity ^ 1] = 0u;
+  if (DIAG) acc.block_reduce_store(p.partials);
+}
+
+}  // namespace elbm

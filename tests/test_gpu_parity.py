@@ -1,0 +1,271 @@
+"""GPU parity of the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances:
+  * FP64 storage, FORMULA / SECANT: every population within 1e-12 relative
+    (the two evaluate the same Eqs. (1)-(9) in FP64; differences are
+    rounding order, FMA contraction and 1-ulp log differences);
+  * FP64 ROOT: the bisection's branch sequence can differ where Delta H(mid)
+    is within rounding of 0 or -1e-13, so the single-step check is that the
+    GPU alpha satisfies the oracle's stop rule, and fields agree to 1e-9;
+  * FP32 storage: velocity L2-relative 1e-5 against the FP64 oracle on
+    laminar flows; per-node alpha never above the FP64 FORMULA alpha of the
+    same stored state and within 1e-4 of it where the state is resolved
+    (the certified decision rounds towards entropy safety);
+  * zero Eq. (7) violations in the FP64 check of every path.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import elbm_workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def elbm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1904_00866_gb300 as e
+    if not os.path.exists(e.LIB_PATH):
+        import __graft_entry__ as g
+        g.build()
+    e.lib()
+    return e
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.lib()
+    return oracle
+
+
+def _pair(elbm, orc, lat, shape, nu, dtype, rho, u):
+    nz, ny, nx = shape
+    g = elbm.Lattice(lat, nx, ny, nz, nu=nu, dtype=dtype)
+    g.init_fields(rho, u)
+    o = orc.Lattice(lat, nx, ny, nz, nu=nu)
+    o.init_fields(rho, u)
+    return g, o
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def test_fp64_taylor_green_64_1000_steps(elbm, orc):
+    """D2Q9 64 x 64 Taylor-Green, nu = 0.01, u0 = 0.05, FP64, FORMULA."""
+    rho, u = W.taylor_green_2d(64, 0.05)
+    g, o = _pair(elbm, orc, "D2Q9", (1, 64, 64), 0.01, "fp64", rho, u)
+    g.set_diagnostics(diag_every=1, check_every=250)
+    g.step(1000, "formula")
+    _, st = o.step(1000, stats=True)
+    f = g.populations()
+    assert np.all(np.abs(f - o.f) <= 1e-12 * np.abs(o.f))
+    s = g.entropy_stats()
+    assert s["step"] == 999 and s["checked"] == 0
+    ref = st[-1]
+    assert abs(s["kinetic_energy"] / ref["kinetic_energy"] - 1) < 1e-11
+    assert abs(s["mass"] - ref["mass"]) < 1e-12 * ref["mass"]
+    assert abs(s["n_accept_two"] - ref["n_accept_two"]) <= 2
+    k2 = 2 * (2 * math.pi / 64) ** 2
+    r, uu = g.moments()
+    e_end = 0.5 * np.sum(r * (uu ** 2).sum(0))
+    assert abs(e_end / st[0]["kinetic_energy"] / math.exp(-2 * 0.01 * k2 * 1000)
+               - 1) < 5e-3
+
+
+@pytest.mark.parametrize("lat,shape", [("D2Q9", (1, 23, 37)),
+                                       ("D3Q27", (11, 13, 19))])
+@pytest.mark.parametrize("mode", ["formula", "secant"])
+def test_fp64_ragged_parity(elbm, orc, lat, shape, mode):
+    nz, ny, nx = shape
+    if lat == "D2Q9":
+        rho, u = W.random_phase_2d(nx, seed=3, umax=0.1, ny=ny)
+    else:
+        rho, u = W.random_phase_3d(nx, seed=3, umax=0.1, ny=ny, nz=nz)
+    g, o = _pair(elbm, orc, lat, shape, 2e-4, "fp64", rho, u)
+    g.set_diagnostics(diag_every=1, check_every=1, alpha_map_every=1)
+    for _ in range(3):
+        g.step(10, mode)
+        amaps, _ = o.step(10, mode, secant_iters=4, alpha_map=True)
+        f = g.populations()
+        assert np.all(np.abs(f - o.f) <= 1e-12 * np.abs(o.f)), _rel(f, o.f)
+        assert np.abs(g.alpha_map() - amaps[-1]).max() < 2e-6   # FP32 map
+    s = g.entropy_stats()
+    assert s["checked"] == 1 and s["n_violations"] == 0
+
+
+@pytest.mark.parametrize("lat,shape", [("D2Q9", (1, 20, 24)),
+                                       ("D3Q27", (6, 7, 9))])
+def test_fp64_root_parity(elbm, orc, lat, shape):
+    nz, ny, nx = shape
+    if lat == "D2Q9":
+        rho, u = W.random_phase_2d(nx, seed=5, umax=0.1, ny=ny)
+    else:
+        rho, u = W.random_phase_3d(nx, seed=5, umax=0.1, ny=ny, nz=nz)
+    g, o = _pair(elbm, orc, lat, shape, 1e-4, "fp64", rho, u)
+    g.set_diagnostics(diag_every=1, check_every=1, alpha_map_every=1)
+    g.step(20, "root")
+    o.step(20, "root")
+    f = g.populations()
+    assert _rel(f, o.f) < 1e-9
+    # one more step: the GPU alpha satisfies the oracle's stop rule
+    f_pre = g.populations().reshape(len(f), -1)
+    g.step(1, "root")
+    amap = g.alpha_map().reshape(-1)
+    c, w = orc.lattice(lat)
+    d = orc.dim(lat)
+    for node in range(0, f_pre.shape[1], max(1, f_pre.shape[1] // 200)):
+        fn = f_pre[:, node]
+        rho_ = fn.sum()
+        feq = orc.equilibrium(lat, rho_, (c[:, :d].T @ fn) / rho_)
+        x = feq / fn - 1
+        a = float(amap[node])   # map is FP32; evaluate at the FP32 value
+        dh = orc.delta_h(fn, x, a)
+        tol = orc.delta_h_bound(fn, x, a) + abs(
+            np.sum(fn * x * (np.log1p(a * x) - np.log1p(x)))) * 1e-7
+        assert dh <= tol
+        assert dh >= -1e-13 - tol or orc.alpha_max(fn, feq) < 2.1
+    s = g.entropy_stats()
+    assert s["n_violations"] == 0 and s["n_root_cap"] == 0
+
+
+@pytest.mark.parametrize("dtype,tol", [("fp32_shifted", 1e-5),
+                                       ("fp32", 2e-4)])
+def test_fp32_taylor_green_2d_vs_fp64_oracle(elbm, orc, dtype, tol):
+    rho, u = W.taylor_green_2d(64, 0.05)
+    g, o = _pair(elbm, orc, "D2Q9", (1, 64, 64), 0.01, dtype, rho, u)
+    g.set_diagnostics(diag_every=1, check_every=100)
+    g.step(1000, "formula")
+    o.step(1000)
+    _, ug = g.moments()
+    _, uo = o.moments()
+    assert np.linalg.norm(ug - uo) / np.linalg.norm(uo) < tol
+    s = g.entropy_stats()
+    assert s["n_violations"] == 0
+
+
+def test_fp32_taylor_green_3d_vs_fp64_oracle(elbm, orc):
+    n = 24
+    rho, u = W.taylor_green_3d(n, 0.05)
+    g, o = _pair(elbm, orc, "D3Q27", (n, n, n), 0.005, "fp32_shifted", rho, u)
+    g.set_diagnostics(diag_every=1, check_every=50)
+    g.step(200, "formula")
+    o.step(200)
+    _, ug = g.moments()
+    _, uo = o.moments()
+    assert np.linalg.norm(ug - uo) / np.linalg.norm(uo) < 1e-5
+    s = g.entropy_stats()
+    assert s["n_violations"] == 0 and s["checked"] == 1
+
+
+@pytest.mark.parametrize("lat,shape,nu", [("D2Q9", (1, 64, 64), 1e-5),
+                                          ("D3Q27", (12, 16, 20), 1e-4)])
+def test_fp32_single_step_alpha_against_fp64(elbm, orc, lat, shape, nu):
+    """One FP32 FORMULA step from an evolved state: per-node alpha vs the
+    FP64 FORMULA alpha of the same stored state, and populations."""
+    nz, ny, nx = shape
+    if lat == "D2Q9":
+        rho, u = W.shear_layer(nx, ny=ny)
+    else:
+        rho, u = W.random_phase_3d(nx, seed=11, umax=0.08, ny=ny, nz=nz)
+    o = orc.Lattice(lat, nx, ny, nz, nu=nu)
+    o.init_fields(rho, u)
+    o.step(60)
+    g = elbm.Lattice(lat, nx, ny, nz, nu=nu, dtype="fp32_shifted")
+    g.set_populations(o.f)
+    g.set_diagnostics(diag_every=1, check_every=1, alpha_map_every=1)
+    loaded = g.populations()          # the state as the GPU stores it
+    o.set_populations(loaded)
+    amaps, st = o.step(1, alpha_map=True, stats=True)
+    g.step(1, "formula")
+    ag = g.alpha_map().astype(np.float64)
+    ao = amaps[0]
+    assert np.all(ag <= ao + 1e-12)
+    close = (ao - ag) <= 1e-4
+    assert close.mean() >= 0.999, close.mean()
+    s = g.entropy_stats()
+    assert s["n_violations"] == 0 and s["checked"] == 1
+    assert s["n_decision_mismatch"] <= s["n_band"]
+    f = g.populations()
+    assert np.all(np.abs(f - o.f) <= 2e-6 * np.abs(o.f))
+
+
+def test_fp32_random_phase_zero_violations(elbm):
+    n = 32
+    rho, u = W.random_phase_3d(n, seed=2, umax=0.05)
+    g = elbm.Lattice("D3Q27", n, n, n, nu=1e-5, dtype="fp32_shifted")
+    g.set_diagnostics(diag_every=1, check_every=1)
+    g.init_fields(rho, u)
+    for _ in range(40):
+        g.step(1, "formula")
+        s = g.entropy_stats()
+        assert s["n_violations"] == 0, s
+    assert s["n_accept_two"] > 0 and s["n_formula"] > 0
+
+
+def test_conservation_on_gpu(elbm):
+    rho, u = W.random_phase_2d(48, seed=4, umax=0.05)
+    for dtype, tol in [("fp64", 1e-13), ("fp32_shifted", 1e-6)]:
+        g = elbm.Lattice("D2Q9", 48, 48, 1, nu=1e-3, dtype=dtype)
+        g.init_fields(rho, u)
+        r0, u0 = g.moments()
+        m0 = r0.sum()
+        p0 = (r0 * u0).reshape(2, -1).sum(1)
+        g.step(200, "formula")
+        r1, u1 = g.moments()
+        assert abs(r1.sum() - m0) <= tol * m0
+        p1 = (r1 * u1).reshape(2, -1).sum(1)
+        assert np.abs(p1 - p0).max() <= tol * m0
+
+
+@pytest.mark.parametrize("lat,shape", [("D2Q9", (1, 1, 1)), ("D2Q9", (1, 1, 5)),
+                                       ("D2Q9", (1, 7, 1)), ("D2Q9", (1, 3, 65)),
+                                       ("D3Q27", (1, 1, 1)), ("D3Q27", (1, 4, 33)),
+                                       ("D3Q27", (5, 1, 3)), ("D3Q27", (2, 3, 1))])
+def test_edge_sizes(elbm, orc, lat, shape):
+    nz, ny, nx = shape
+    d = orc.dim(lat)
+    rng = np.random.default_rng(sum(shape))
+    rho = 1.0 + 0.02 * rng.uniform(-1, 1, size=shape)
+    u = 0.05 * rng.uniform(-1, 1, size=(d,) + shape)
+    for mode in ["formula", "root"]:
+        g, o = _pair(elbm, orc, lat, shape, 1e-3, "fp64", rho, u)
+        g.step(7, mode)
+        o.step(7, mode)
+        assert _rel(g.populations(), o.f) < (1e-12 if mode == "formula" else 1e-9)
+
+
+def test_invalid_inputs_are_rejected(elbm):
+    g = elbm.Lattice("D2Q9", 8, 8, 1, nu=0.01, dtype="fp32_shifted")
+    rho = np.ones((1, 8, 8))
+    u = np.zeros((2, 1, 8, 8))
+    u[0, 0, 0, 0] = 1.0
+    with pytest.raises(elbm.ElbmError) as e:
+        g.init_fields(rho, u)
+    assert e.value.status == 1
+    with pytest.raises(elbm.ElbmError):
+        g.alpha_map()            # nothing written yet
+    f = np.full((9, 1, 8, 8), 0.1)
+    f[3, 0, 2, 2] = 0.0
+    with pytest.raises(elbm.ElbmError):
+        g.set_populations(f)
+    with pytest.raises(elbm.ElbmError):
+        g.step(1, 9)
+
+
+def test_device_resident_init_matches_host_init(elbm):
+    import torch
+    rho, u = W.taylor_green_3d(16, 0.05)
+    a = elbm.Lattice("D3Q27", 16, 16, 16, nu=0.01, dtype="fp32_shifted")
+    a.init_fields(rho, u)
+    b = elbm.Lattice("D3Q27", 16, 16, 16, nu=0.01, dtype="fp32_shifted")
+    b.init_fields(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
+    a.step(5)
+    b.step(5)
+    assert np.array_equal(a.populations(), b.populations())
