@@ -1,0 +1,441 @@
+#!/usr/bin/env python
+"""Benchmark of the ELBM hot path on GB300.
+
+Default workload (one JSON line on stdout): D3Q27 periodic Taylor-Green
+vortex 512^3, Re = 1600, u0 = 0.05 (nu = u0 (N / 2 pi) / 1600), populations
+stored in FP32 as deviations from W_i rho0, FORMULA alpha (Eqs. (8)-(9)).
+A step is one Eq. (1) update of the whole lattice (gather, collide,
+relax, store, fused diagnostics on the configured interval).
+
+  value        MLUPS (10^6 lattice-node updates / s), device-timed with CUDA
+               events on the library's stream, inputs resident in HBM;
+  e2e          same metric through the public API with host buffers: the
+               timed region holds elbm_init_fields from pinned host memory,
+               the K steps, the per-step statistics read-back and the final
+               moments read-back;
+  roofline     the stream-collide kernel: algorithmic bytes per launch
+               (27 x 4 B read + 27 x 4 B written per node) / its average
+               CUDA-event duration, against the measured HBM copy peak;
+  secondary    FORMULA vs ROOT and FP32 vs FP64 on 256^3 D3Q27 and on the
+               1024^2 D2Q9 double shear layer (not the headline);
+  cpu_baseline the CPU FP64 oracle on a bounded sample (64^3 D3Q27 TGV).
+
+--impl reference times the CPU oracle itself (the only reference this
+method has) on bounded samples of the same workload.  Multi-GPU runs
+(torchrun) execute independent replicas: no data exchange.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_MAIN = 512
+U0 = 0.05
+RE = 1600.0
+BYTES_PER_LU = {("D3Q27", 4): 216, ("D3Q27", 8): 432, ("D2Q9", 4): 72,
+                ("D2Q9", 8): 144}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def nu_for(n):
+    return U0 * (n / (2 * math.pi)) / RE
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="elbm", choices=["elbm", "reference"])
+    ap.add_argument("--n", type=int, default=N_MAIN)
+    ap.add_argument("--diag-every", type=int, default=10)
+    ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons (200 ms)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,"
+         "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", delete=False,
+                                                    suffix=".csv")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for line in self.file.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        os.unlink(self.file.name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_lattice(elbm, lat, n, dtype, nu, rho_dev=None, u_dev=None):
+    import torch
+    import elbm_workloads as W
+    nz = n if lat == "D3Q27" else 1
+    g = elbm.Lattice(lat, n, n, nz, nu=nu, dtype=dtype)
+    if rho_dev is None:
+        if lat == "D3Q27":
+            rho, u = W.taylor_green_3d(n, U0)
+        else:
+            rho, u = W.shear_layer(n)
+        rho_dev = torch.from_numpy(rho).cuda()
+        u_dev = torch.from_numpy(u).cuda()
+    g.init_fields(rho_dev, u_dev)
+    return g
+
+
+def time_steps(g, steps, mode, stream):
+    """Device time (ms) of `steps` steps, and stream-collide kernel time."""
+    import torch
+    g.sync()
+    g.set_profiling(True)
+    g.profile()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(steps, mode)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    kms, nk = g.profile()
+    g.set_profiling(False)
+    g.sync()
+    return ms, kms, nk
+
+
+def secondary(elbm, stream):
+    """FORMULA vs ROOT, FP32 vs FP64 (MLUPS), on smaller lattices."""
+    out = {}
+    n3 = 256
+    for key, dtype, mode, steps in [
+            ("d3q27_256_fp32_formula", "fp32_shifted", "formula", 20),
+            ("d3q27_256_fp64_formula", "fp64", "formula", 3),
+            ("d3q27_256_fp32_root", "fp32_shifted", "root", 1)]:
+        g = make_lattice(elbm, "D3Q27", n3, dtype, nu_for(n3))
+        g.set_diagnostics(diag_every=0)
+        g.step(1, mode)
+        ms, kms, nk = time_steps(g, steps, mode, stream)
+        out[key] = round(n3 ** 3 * steps / (ms * 1e3), 1)
+        g.close()
+    n2 = 1024
+    nu2 = 0.04 * n2 / 30000.0
+    for key, dtype, mode, steps in [
+            ("d2q9_1024_fp32_formula", "fp32_shifted", "formula", 200),
+            ("d2q9_1024_fp64_formula", "fp64", "formula", 20),
+            ("d2q9_1024_fp32_root", "fp32_shifted", "root", 5)]:
+        g = make_lattice(elbm, "D2Q9", n2, dtype, nu2)
+        g.set_diagnostics(diag_every=0)
+        g.step(2, mode)
+        ms, kms, nk = time_steps(g, steps, mode, stream)
+        out[key] = round(n2 * n2 * steps / (ms * 1e3), 1)
+        g.close()
+    out["unit"] = "MLUPS"
+    out["speedup_formula_vs_root_d3q27_fp32"] = round(
+        out["d3q27_256_fp32_formula"] / out["d3q27_256_fp32_root"], 1)
+    out["speedup_formula_vs_root_d2q9_fp32"] = round(
+        out["d2q9_1024_fp32_formula"] / out["d2q9_1024_fp32_root"], 1)
+    return out
+
+
+def cpu_baseline(target_s=12.0):
+    """The CPU FP64 oracle, as it stands, on a bounded D3Q27 TGV sample."""
+    import oracle
+    import elbm_workloads as W
+    n = 64
+    threads = os.cpu_count() or 1
+    rho, u = W.taylor_green_3d(n, U0)
+    o = oracle.Lattice("D3Q27", n, n, n, nu=nu_for(n))
+    o.init_fields(rho, u)
+    t0 = time.perf_counter()
+    o.step(1, threads=threads)
+    t1 = time.perf_counter()
+    steps = max(1, int(target_s / max(t1 - t0, 1e-3)))
+    t0 = time.perf_counter()
+    o.step(steps, threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": round(n ** 3 * steps / dt / 1e6, 3), "unit": "MLUPS",
+            "cores": threads, "kind": "oracle",
+            "sample": "D3Q27 %d^3 Taylor-Green, FORMULA, FP64, %d steps "
+                      "(%.1f s)" % (n, steps, dt)}
+
+
+def run_elbm(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    import paper_1904_00866_gb300 as elbm
+    if not os.path.exists(elbm.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    torch.cuda.init()
+    stream = torch.cuda.current_stream()
+    n = args.n
+    nu = nu_for(n)
+    g = make_lattice(elbm, "D3Q27", n, "fp32_shifted", nu)
+    g.set_diagnostics(diag_every=args.diag_every)
+    g.step(args.warmup, "formula")
+    g.sync()
+    barrier(world)
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    l0 = elbm.launch_count()
+    ms, kms, nk = time_steps(g, args.steps, "formula", stream)
+    launches = elbm.launch_count() - l0
+    ck = clocks.stop()
+    barrier(world)
+    ms = max_over_ranks(ms, world)
+    nodes = n ** 3
+    value = nodes * args.steps * world / (ms * 1e3)
+    hbm, hbm_kind = peaks()
+    kernel_ms = kms / max(nk, 1)
+    achieved = BYTES_PER_LU[("D3Q27", 4)] * nodes / (kernel_ms * 1e-3) / 1e9
+    # one checked step (untimed): violations and decision statistics
+    g.set_diagnostics(diag_every=1, check_every=1)
+    g.step(1, "formula")
+    st = g.entropy_stats()
+    result = {
+        "metric": "MLUPS (D3Q27 FORMULA FP32-shifted)",
+        "value": round(value, 1),
+        "unit": "MLUPS",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {
+            "workload": "D3Q27 periodic Taylor-Green vortex %d^3, Re=1600, "
+                        "u0=0.05, nu=%.4g, FP32 populations stored as "
+                        "f - W rho0, alpha FORMULA" % (n, nu),
+            "nodes": nodes,
+            "diag_every": args.diag_every,
+            "l2": "inputs larger than L2 (%.1f GB of populations read per "
+                  "step vs 129 MB L2); no flush" % (nodes * 108 / 1e9),
+            "parallelism": "replicas" if world > 1 else "single GPU",
+        },
+        "roofline": {
+            "bound": "hbm",
+            "kernel": "k_stream_collide<D3Q27,float,FORMULA>",
+            "achieved": round(achieved, 1),
+            "peak": hbm,
+            "peak_kind": hbm_kind,
+            "unit": "GB/s",
+            "frac": round(achieved / hbm, 4),
+            "bytes_per_launch": BYTES_PER_LU[("D3Q27", 4)] * nodes,
+            "kernel_ms": round(kernel_ms, 4),
+            "traffic": None,
+        },
+        "gpu_launches": launches,
+        "clocks": ck,
+        "entropy_check": {
+            "step": st["step"], "n_violations": st["n_violations"],
+            "n_accept_two": st["n_accept_two"], "n_formula": st["n_formula"],
+            "n_band": st["n_band"], "n_far": st["n_far"],
+            "n_decision_mismatch": st["n_decision_mismatch"],
+            "alpha_dev_max": st["alpha_dev_max"],
+            "alpha_min": st["alpha_min"],
+        },
+    }
+    g.close()
+    torch.cuda.empty_cache()
+    if not args.no_e2e:
+        result["e2e"] = e2e(elbm, args, n, nu, stream, world)
+    if not args.no_secondary and rank == 0:
+        result["secondary"] = secondary(elbm, stream)
+    if not args.no_cpu and rank == 0 and world == 1:
+        result["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(result))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def e2e(elbm, args, n, nu, stream, world):
+    """Public-API run with host buffers: pinned H2D of the initial fields,
+    K steps with the statistics read back every step, D2H of the final
+    moments -- all inside the timed region."""
+    import numpy as np
+    import torch
+    import elbm_workloads as W
+    rho, u = W.taylor_green_3d(n, U0)
+    rho_h = torch.empty(rho.shape, dtype=torch.float64, pin_memory=True)
+    u_h = torch.empty(u.shape, dtype=torch.float64, pin_memory=True)
+    rho_h.numpy()[...] = rho
+    u_h.numpy()[...] = u
+    del rho, u
+    out_rho = torch.empty(rho_h.shape, dtype=torch.float64, pin_memory=True)
+    out_u = torch.empty(u_h.shape, dtype=torch.float64, pin_memory=True)
+    g = elbm.Lattice("D3Q27", n, n, n, nu=nu, dtype="fp32_shifted")
+    g.set_diagnostics(diag_every=1)
+    g.init_fields(rho_h.numpy(), u_h.numpy())     # allocate once, untimed
+    g.step(args.warmup, "formula")
+    g.sync()
+    barrier(world)
+    t0 = time.perf_counter()
+    g.init_fields(rho_h.numpy(), u_h.numpy())
+    for _ in range(args.steps):
+        g.step(1, "formula")
+        g.entropy_stats()
+    import ctypes
+    st = elbm.lib().elbm_moments(
+        g._h, ctypes.cast(out_rho.data_ptr(), elbm._DP),
+        ctypes.cast(out_u.data_ptr(), elbm._DP))
+    if st:
+        raise RuntimeError("moments failed")
+    dt = time.perf_counter() - t0
+    dt = max_over_ranks(dt, world)
+    g.close()
+    nodes = n ** 3
+    stats_bytes = 200
+    return {"value": round(nodes * args.steps * world / dt / 1e6, 1),
+            "unit": "MLUPS",
+            "h2d_bytes_per_step": int(rho_h.numel() * 8 + u_h.numel() * 8)
+            // args.steps,
+            "d2h_bytes_per_step": int((out_rho.numel() + out_u.numel()) * 8)
+            // args.steps + stats_bytes,
+            "seconds": round(dt, 3)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import elbm_workloads as W
+    n = 48      # bounded sample of the 512^3 workload: one 48^3 block
+    threads = os.cpu_count() or 1
+    rho, u = W.taylor_green_3d(n, U0)
+    o = oracle.Lattice("D3Q27", n, n, n, nu=nu_for(args.n))
+    o.init_fields(rho, u)
+    o.step(args.warmup, threads=threads)
+    t0 = time.perf_counter()
+    o.step(args.steps, threads=threads)
+    dt = time.perf_counter() - t0
+    value = n ** 3 * args.steps / dt / 1e6
+    print(json.dumps({
+        "impl": "reference",
+        "metric": "MLUPS (D3Q27 FORMULA FP32-shifted)",
+        "value": round(value, 3), "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt * 1e3 / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "D3Q27 periodic Taylor-Green vortex, Re=1600, "
+                               "u0=0.05, nu=%.4g; each step a bounded %d^3 "
+                               "sample of the %d^3 lattice" % (
+                                   nu_for(args.n), n, args.n)},
+        "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS",
+                         "cores": threads, "kind": "oracle",
+                         "sample": "%d^3 D3Q27 block per step, FP64 CPU "
+                                   "oracle" % n},
+        "e2e": {"value": round(value, 3), "unit": "MLUPS",
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_elbm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -215,6 +215,15 @@ ELBM_API size_t elbm_device_bytes(const elbm_handle *h);
  * (all handles).  Used to account the work of a timed region. */
 ELBM_API long long elbm_launch_count(void);
 
+/* Record CUDA events (on the handle's stream) around every stream-collide
+ * kernel launch while enable != 0. */
+ELBM_API elbm_status elbm_set_profiling(elbm_handle *h, int enable);
+
+/* Total device time (ms) and number of the stream-collide launches recorded
+ * since the last call; resets the record.  Synchronises. */
+ELBM_API elbm_status elbm_profile(elbm_handle *h, double *stream_collide_ms,
+                                  long long *launches);
+
 /* Reference density rho0 of the shifted storage (meaningful after init). */
 ELBM_API double elbm_rho0(const elbm_handle *h);
 

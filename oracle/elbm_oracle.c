@@ -248,6 +248,10 @@ static double alpha_formula(int q, const double *f, const double *x,
   /* H(f*(alpha_*)) - H(f^eq) = D_* - Delta H(1), since f*(1) = f^eq. */
   double d_one = orc_delta_h(q, f, x, 1.0);
   *flags |= ORC_F_FORMULA;
+  /* d_star - d_one = H(f*(alpha_*)) - H(f^eq) > 0 in exact arithmetic; a
+   * non-positive value means f equals f^eq to rounding: take alpha = 1
+   * (f* = f^eq). */
+  if (!(d_star - d_one > 0.0)) return 1.0;
   return alpha_star + d_star / (d_star - d_one) * (1.0 - alpha_star);
 }
 
@@ -291,11 +295,18 @@ static double alpha_secant(int q, const double *f, const double *x,
   *flags |= ORC_F_FORMULA;
   double a = 1.0;
   double d_a = orc_delta_h(q, f, x, a);
+  if (!(d_star - d_a > 0.0)) return 1.0; /* f == f^eq to rounding */
+  /* The iterates keep Delta H <= 0 in exact arithmetic; an iterate whose
+   * computed Delta H is positive (rounding) ends the iteration at the
+   * previous iterate. */
   for (int k = 0; k < n_iter; k++) {
-    a = alpha_star + d_star / (d_star - d_a) * (a - alpha_star);
+    double a_next = alpha_star + d_star / (d_star - d_a) * (a - alpha_star);
+    double d_next = orc_delta_h(q, f, x, a_next);
     (*iters)++;
-    d_a = orc_delta_h(q, f, x, a);
-    if (d_a >= -ROOT_TOL && d_a <= 0.0) break;
+    if (d_next > 0.0) break;
+    a = a_next;
+    d_a = d_next;
+    if (d_a >= -ROOT_TOL) break;
   }
   return a;
 }

@@ -114,6 +114,8 @@ SIGNATURES = {
     "elbm_device_bytes": (ctypes.c_size_t, [_P]),
     "elbm_launch_count": (ctypes.c_longlong, []),
     "elbm_rho0": (ctypes.c_double, [_P]),
+    "elbm_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
+    "elbm_profile": (ctypes.c_int, [_P, _DP, _LLP]),
 }
 
 
@@ -296,6 +298,18 @@ class Lattice:
         s = EntropyStats()
         self._check(lib().elbm_entropy_stats(self._h, ctypes.byref(s)))
         return s.as_dict()
+
+    def set_profiling(self, enable=True):
+        self._check(lib().elbm_set_profiling(self._h, int(bool(enable))))
+
+    def profile(self):
+        """(total ms, launches) of the stream-collide kernels recorded since
+        the last call."""
+        ms = ctypes.c_double()
+        n = ctypes.c_longlong()
+        self._check(lib().elbm_profile(self._h, ctypes.byref(ms),
+                                       ctypes.byref(n)))
+        return ms.value, n.value
 
     @property
     def step_count(self):

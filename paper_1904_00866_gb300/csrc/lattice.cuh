@@ -7,18 +7,6 @@
 // component and weight is a compile-time constant.
 #pragma once
 
-// (2/3)^(D-k) (1/6)^k = 2^(D-k) / (3^(D-k) 6^k)
-template <int D>
-__host__ __device__ constexpr double weight(int k) {
-  long long num = 1, den = 1;
-  for (int a = 0; a < D - k; ++a) {
-    num *= 2;
-    den *= 3;
-  }
-  for (int a = 0; a < k; ++a) den *= 6;
-  return (double)num / (double)den;
-}
-
 struct D2Q9 {
   static constexpr int D = 2;
   static constexpr int Q = 9;
@@ -28,10 +16,16 @@ struct D2Q9 {
                              {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}};
     return t[i][a];
   }
-  // product of the per-axis D1Q3 weights, (2/3)^(D-k) (1/6)^k for k
-  // nonzero components, as one correctly rounded quotient of integers
+  // product of the per-axis D1Q3 weights, (2/3)^(2-k) (1/6)^k for k
+  // nonzero components; literal fractions fold to correctly rounded
+  // constants at compile time
   __host__ __device__ static constexpr double w(int i) {
-    return weight<D>(nonzero(i));
+    return nonzero(i) == 0 ? 4.0 / 9.0
+                           : (nonzero(i) == 1 ? 1.0 / 9.0 : 1.0 / 36.0);
+  }
+  __host__ __device__ static constexpr float wf(int i) {
+    return nonzero(i) == 0 ? 4.0f / 9.0f
+                           : (nonzero(i) == 1 ? 1.0f / 9.0f : 1.0f / 36.0f);
   }
   __host__ __device__ static constexpr int nonzero(int i) {
     return (c(i, 0) != 0) + (c(i, 1) != 0) + (c(i, 2) != 0);
@@ -51,8 +45,20 @@ struct D3Q27 {
         {-1, 1, 1},   {1, -1, -1}};
     return t[i][a];
   }
+  // (2/3)^(3-k) (1/6)^k for k nonzero components (literal fractions)
   __host__ __device__ static constexpr double w(int i) {
-    return weight<D>(nonzero(i));
+    return nonzero(i) == 0
+               ? 8.0 / 27.0
+               : (nonzero(i) == 1 ? 2.0 / 27.0
+                                  : (nonzero(i) == 2 ? 1.0 / 54.0
+                                                     : 1.0 / 216.0));
+  }
+  __host__ __device__ static constexpr float wf(int i) {
+    return nonzero(i) == 0
+               ? 8.0f / 27.0f
+               : (nonzero(i) == 1 ? 2.0f / 27.0f
+                                  : (nonzero(i) == 2 ? 1.0f / 54.0f
+                                                     : 1.0f / 216.0f));
   }
   __host__ __device__ static constexpr int nonzero(int i) {
     return (c(i, 0) != 0) + (c(i, 1) != 0) + (c(i, 2) != 0);

@@ -2,6 +2,7 @@
 // instantiates the subset it owns so the kernels compile in parallel.
 #pragma once
 #include "internal.h"
+#include "sc32.cuh"
 
 namespace elbm {
 
@@ -12,6 +13,7 @@ static int occupancy_grid(Kernel k, int block, long long threads_needed) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, 0);
   if (per_sm < 1) per_sm = 1;
+  if (per_sm > 2048 / block) per_sm = 2048 / block;   // partials rows bound
   long long g = (long long)sms * per_sm;
   const long long need = (threads_needed + block - 1) / block;
   if (need < g) g = need;
@@ -50,6 +52,44 @@ static cudaError_t launch_fp64_modes(int mode, int diag, int check,
                                           grid_used);
   return launch_diag<L, T, MODE_FORMULA>(diag, check, p, grid, block, s,
                                          grid_used);
+}
+
+// Pipelined FP32 FORMULA kernel (dynamic shared memory: 2 stages x Q x 256).
+template <class L, int DIAG, int CHECK>
+static cudaError_t launch_sc32_one(const StepParams& p, int grid,
+                                   cudaStream_t s, int* grid_used) {
+  auto k = k_sc32<L, DIAG, CHECK>;
+  const int smem = 2 * L::Q * kSc32Threads * (int)sizeof(float);
+  static bool configured = false;   // per instantiation
+  if (!configured) {
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    configured = true;
+  }
+  if (grid <= 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kSc32Threads,
+                                                  smem);
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 2048 / kSc32Threads) per_sm = 2048 / kSc32Threads;
+    long long g = (long long)sms * per_sm;
+    const long long tiles = (p.n + kSc32Threads - 1) / kSc32Threads;
+    if (tiles < g) g = tiles;
+    grid = g < 1 ? 1 : (int)g;
+  }
+  if (grid_used) *grid_used = grid;
+  k<<<grid, kSc32Threads, smem, s>>>(p);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <class L>
+static cudaError_t launch_sc32(int diag, int check, const StepParams& p,
+                               int grid, cudaStream_t s, int* grid_used) {
+  if (check) return launch_sc32_one<L, 1, 1>(p, grid, s, grid_used);
+  if (diag) return launch_sc32_one<L, 1, 0>(p, grid, s, grid_used);
+  return launch_sc32_one<L, 0, 0>(p, grid, s, grid_used);
 }
 
 // The fixup grid must equal the grid of the FP32 step when DIAG is set (its

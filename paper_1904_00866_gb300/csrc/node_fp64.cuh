@@ -37,19 +37,28 @@ enum : unsigned {
 
 enum { MODE_FORMULA = 0, MODE_ROOT = 1, MODE_SECANT = 2 };
 
-__host__ __device__ constexpr double phi_coef(int k) {
-  return ((k % 2 == 0) ? 1.0 : -1.0) / (double)(k * (k - 1));
-}
-
 // phi(y) = (1 + y) ln(1 + y) - y for y >= -1 (phi(-1) = 1, 0 ln 0 := 0).
-// |y| < 0.1: y^2 sum_{k=2}^{17} (-1)^k y^(k-2) / (k (k-1)) (Horner); the
-// first omitted term is below 1e-18 of the sum.
+// |y| < 0.1: y^2 sum_{k=2}^{17} (-1)^k y^(k-2) / (k (k-1)) (Horner, literal
+// coefficients); the first omitted term is below 1e-18 of the sum.
 __device__ __forceinline__ double phi64(double y) {
   if (y <= -1.0) return 1.0;
   if (fabs(y) < 0.1) {
-    double s = phi_coef(17);
-#pragma unroll
-    for (int k = 16; k >= 2; --k) s = fma(s, y, phi_coef(k));
+    double s = -1.0 / 272.0;                // k = 17
+    s = fma(s, y, 1.0 / 240.0);             // 16
+    s = fma(s, y, -1.0 / 210.0);            // 15
+    s = fma(s, y, 1.0 / 182.0);             // 14
+    s = fma(s, y, -1.0 / 156.0);            // 13
+    s = fma(s, y, 1.0 / 132.0);             // 12
+    s = fma(s, y, -1.0 / 110.0);            // 11
+    s = fma(s, y, 1.0 / 90.0);              // 10
+    s = fma(s, y, -1.0 / 72.0);             // 9
+    s = fma(s, y, 1.0 / 56.0);              // 8
+    s = fma(s, y, -1.0 / 42.0);             // 7
+    s = fma(s, y, 1.0 / 30.0);              // 6
+    s = fma(s, y, -1.0 / 20.0);             // 5
+    s = fma(s, y, 1.0 / 12.0);              // 4
+    s = fma(s, y, -1.0 / 6.0);              // 3
+    s = fma(s, y, 1.0 / 2.0);               // 2
     return y * y * s;
   }
   return (1.0 + y) * log1p(y) - y;
@@ -146,7 +155,10 @@ __device__ __forceinline__ double alpha_formula64(const Node64<L>& s,
     return astar;
   }
   flags |= NF_FORMULA;
-  // H(f*(alpha_*)) - H(f^eq) = Delta H(alpha_*) - Delta H(1)
+  // H(f*(alpha_*)) - H(f^eq) = Delta H(alpha_*) - Delta H(1) > 0 in exact
+  // arithmetic; a non-positive value means f equals f^eq to rounding, where
+  // alpha = 1 (f* = f^eq) is taken.
+  if (!(Dstar - D1 > 0.0)) return 1.0;
   return astar + Dstar / (Dstar - D1) * (1.0 - astar);
 }
 
@@ -197,12 +209,19 @@ __device__ __forceinline__ double alpha_secant64(const Node64<L>& s,
     return astar;
   }
   flags |= NF_FORMULA;
+  if (!(Dstar - D1 > 0.0)) return 1.0;   // f == f^eq to rounding
+  // Every iterate keeps Delta H <= 0 in exact arithmetic; an iterate whose
+  // computed Delta H is positive (rounding) ends the iteration at the
+  // previous one.
   double a = 1.0, da = D1;
   for (int k = 0; k < n_iter; ++k) {
-    a = astar + Dstar / (Dstar - da) * (a - astar);
+    const double an = astar + Dstar / (Dstar - da) * (a - astar);
+    const double dn = dH64_phi_sum(s, an) - an * B;
     ++iters;
-    da = dH64_phi_sum(s, a) - a * B;
-    if (da >= -kRootTol && da <= 0.0) break;
+    if (dn > 0.0) break;
+    a = an;
+    da = dn;
+    if (da >= -kRootTol) break;
   }
   return a;
 }

@@ -205,6 +205,23 @@ __global__ void k_finish(const double* __restrict__ partials, int rows,
   if (threadIdx.x == 0) out[k] = sm[0];
 }
 
+// Block partial sums of x[0..n) (one row per block, fixed order).
+__global__ void k_partial_sum(const double* __restrict__ x, long long n,
+                              double* __restrict__ partials) {
+  __shared__ double sm[256];
+  double v = 0.0;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x)
+    v += x[k];
+  sm[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = sm[0];
+}
+
 }  // namespace elbm
 
 using namespace elbm;
@@ -240,6 +257,9 @@ struct elbm_handle {
   long long stats_step = 0;
   int stats_checked = 0;
   size_t bytes = 0;
+  bool profiling = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+  size_t events_used = 0;
   std::vector<std::pair<void*, size_t>> owned;
   std::string err;
 };
@@ -418,6 +438,10 @@ elbm_status elbm_create(elbm_handle** out, elbm_lattice lattice, int nx,
 void elbm_destroy(elbm_handle* h) {
   if (!h) return;
   if (!h->owned.empty()) cudaStreamSynchronize(h->stream);
+  for (auto& ev : h->events) {
+    cudaEventDestroy(ev.first);
+    cudaEventDestroy(ev.second);
+  }
   while (!h->owned.empty()) dev_free(h, h->owned.back().first);
   delete h;
 }
@@ -459,11 +483,33 @@ elbm_status elbm_set_diagnostics(elbm_handle* h, int diag_every,
   return ELBM_OK;
 }
 
+// Mean of a device array (deterministic: fixed grid, rows summed in order
+// on the host).
+static elbm_status device_mean(elbm_handle* h, const double* x, double* mean) {
+  const int grid = grid_for(h->n);
+  k_partial_sum<<<grid, 256, 0, h->stream>>>(x, h->n, h->partials);
+  count_launch();
+  std::vector<double> rows(grid);
+  cudaError_t e = cudaMemcpyAsync(rows.data(), h->partials,
+                                  sizeof(double) * grid,
+                                  cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "density mean");
+  double s = 0.0;
+  for (double r : rows) s += r;
+  *mean = s / (double)h->n;
+  return ELBM_OK;
+}
+
+// f^0 = f^eq(rho, u) from device fields; rho0 = FP32-rounded mean density.
 static elbm_status init_common(elbm_handle* h, const double* rho_dev,
-                               const double* u_dev, double rho_mean) {
-  h->rho0 = (double)(float)rho_mean;
-  elbm_status st = ensure_buffers(h);
+                               const double* u_dev) {
+  double mean = 1.0;
+  elbm_status st = device_mean(h, rho_dev, &mean);
   if (st) return st;
+  if (!(mean > 0.0) || !(mean < 1e30))
+    return fail(h, ELBM_EINVAL, "rho must be > 0 and finite");
+  h->rho0 = (double)(float)mean;
   cudaMemsetAsync(h->err_flags, 0, 256, h->stream);
   cudaMemsetAsync(h->far_count, 0, 256, h->stream);
   h->cur = 0;
@@ -474,20 +520,16 @@ static elbm_status init_common(elbm_handle* h, const double* rho_dev,
   h->alpha_map_valid = false;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "init kernel");
-  return ELBM_OK;
+  st = check_errors(h);
+  if (st == ELBM_ENONFINITE || st == ELBM_ENEGATIVE)
+    return fail(h, ELBM_EINVAL, "invalid initial fields (rho <= 0, "
+                                "non-finite, or |u| >= 1)");
+  return st;
 }
 
 elbm_status elbm_init_fields(elbm_handle* h, const double* rho,
                              const double* u) {
   if (!h || !rho || !u) return h ? fail(h, ELBM_EINVAL, "NULL field") : ELBM_EINVAL;
-  double sum = 0.0;
-  for (long long k = 0; k < h->n; ++k) {
-    if (!(rho[k] > 0.0)) return fail(h, ELBM_EINVAL, "rho must be > 0");
-    sum += rho[k];
-  }
-  for (long long k = 0; k < (long long)h->d * h->n; ++k)
-    if (!(u[k] > -1.0 && u[k] < 1.0))
-      return fail(h, ELBM_EINVAL, "|u| must be < 1");
   elbm_status st = ensure_buffers(h);
   if (st) return st;
   const size_t bytes = sizeof(double) * (1 + h->d) * h->n;
@@ -499,33 +541,22 @@ elbm_status elbm_init_fields(elbm_handle* h, const double* rho,
     e = cudaMemcpyAsync(tmp + h->n, u, sizeof(double) * h->d * h->n,
                         cudaMemcpyHostToDevice, h->stream);
   if (e != cudaSuccess) {
+    cudaStreamSynchronize(h->stream);
     dev_free(h, tmp);
     return cuda_fail(h, e, "copy fields");
   }
-  st = init_common(h, tmp, tmp + h->n, sum / (double)h->n);
+  st = init_common(h, tmp, tmp + h->n);
   cudaStreamSynchronize(h->stream);
   dev_free(h, tmp);
-  if (st) return st;
-  return check_errors(h);
+  return st;
 }
 
 elbm_status elbm_init_fields_device(elbm_handle* h, const double* rho_device,
                                     const double* u_device) {
   if (!h || !rho_device || !u_device) return h ? fail(h, ELBM_EINVAL, "NULL field") : ELBM_EINVAL;
-  // rho0 from a strided host sample of the density (rounded to FP32 anyway)
-  const long long stride = h->n > 4096 ? h->n / 4096 : 1;
-  std::vector<double> sample;
-  for (long long k = 0; k < h->n; k += stride) {
-    double v = 0.0;
-    cudaMemcpy(&v, rho_device + k, sizeof(double), cudaMemcpyDeviceToHost);
-    sample.push_back(v);
-  }
-  double sum = 0.0;
-  for (double v : sample) sum += v;
-  elbm_status st = init_common(h, rho_device, u_device,
-                               sum / (double)sample.size());
+  elbm_status st = ensure_buffers(h);
   if (st) return st;
-  return check_errors(h);
+  return init_common(h, rho_device, u_device);
 }
 
 elbm_status elbm_set_populations(elbm_handle* h, const double* f) {
@@ -595,10 +626,17 @@ elbm_status elbm_step(elbm_handle* h, long long nsteps, elbm_alpha_mode mode) {
     p.corr_rho = (float)(ssum - h->rho0);
   }
   p.secant_iters = h->secant_iters;
+  p.div_nx.init((unsigned)h->nx);
+  p.div_ny.init((unsigned)h->ny);
   p.partials = h->partials;
   p.err_flags = h->err_flags;
   p.far_count = h->far_count;
   p.far_queue = h->far_queue;
+  p.far_cap = h->far_queue ? (unsigned)h->n : 0u;
+  // the deferred-node counters start every call at zero; within the call
+  // each step's fixup clears the counter the next step uses
+  if (nsteps > 0) cudaMemsetAsync(h->far_count, 0, 2 * sizeof(unsigned),
+                                  h->stream);
   const bool d2 = h->lattice == ELBM_D2Q9;
   const int storage = h->dtype == ELBM_FP64 ? 0 : 1;
   for (long long s = 0; s < nsteps; ++s) {
@@ -613,6 +651,17 @@ elbm_status elbm_step(elbm_handle* h, long long nsteps, elbm_alpha_mode mode) {
     int grid = 0;
     cudaError_t e;
     const bool fp32_formula = storage == 1 && mode == ELBM_ALPHA_FORMULA;
+    std::pair<cudaEvent_t, cudaEvent_t>* ev = nullptr;
+    if (h->profiling) {
+      if (h->events_used == h->events.size()) {
+        std::pair<cudaEvent_t, cudaEvent_t> pr;
+        cudaEventCreate(&pr.first);
+        cudaEventCreate(&pr.second);
+        h->events.push_back(pr);
+      }
+      ev = &h->events[h->events_used++];
+      cudaEventRecord(ev->first, h->stream);
+    }
     if (storage == 0)
       e = d2 ? launch_fp64_d2q9(mode, diag, check, p, 0, 256, h->stream, &grid)
              : launch_fp64_d3q27(mode, diag, check, p, 0, 256, h->stream, &grid);
@@ -626,6 +675,7 @@ elbm_status elbm_step(elbm_handle* h, long long nsteps, elbm_alpha_mode mode) {
              : launch_fp32_fp64mode_d3q27(mode, diag, check, p, 0, 256,
                                           h->stream, &grid);
     if (e != cudaSuccess) return cuda_fail(h, e, "stream-collide launch");
+    if (ev) cudaEventRecord(ev->second, h->stream);
     int rows = grid;
     if (fp32_formula) {
       StepParams pf = p;
@@ -785,5 +835,28 @@ size_t elbm_device_bytes(const elbm_handle* h) { return h ? h->bytes : 0; }
 long long elbm_launch_count(void) { return g_launches.load(); }
 
 double elbm_rho0(const elbm_handle* h) { return h ? h->rho0 : 0.0; }
+
+elbm_status elbm_set_profiling(elbm_handle* h, int enable) {
+  if (!h) return ELBM_EINVAL;
+  h->profiling = enable != 0;
+  return ELBM_OK;
+}
+
+elbm_status elbm_profile(elbm_handle* h, double* ms, long long* launches) {
+  if (!h) return ELBM_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "stream synchronize");
+  double total = 0.0;
+  for (size_t k = 0; k < h->events_used; ++k) {
+    float t = 0.0f;
+    e = cudaEventElapsedTime(&t, h->events[k].first, h->events[k].second);
+    if (e != cudaSuccess) return cuda_fail(h, e, "event elapsed time");
+    total += t;
+  }
+  if (ms) *ms = total;
+  if (launches) *launches = (long long)h->events_used;
+  h->events_used = 0;
+  return ELBM_OK;
+}
 
 }  // extern "C"

@@ -5,8 +5,8 @@ namespace elbm {
 cudaError_t launch_fp32_formula_d2q9(int diag, int check, const StepParams& p,
                                       int grid, int block, cudaStream_t s,
                                       int* grid_used) {
-  return launch_diag<D2Q9, float, MODE_FORMULA>(diag, check, p, grid, block, s,
-                                                  grid_used);
+  (void)block;
+  return launch_sc32<D2Q9>(diag, check, p, grid, s, grid_used);
 }
 cudaError_t launch_far_d2q9(int diag, int check, const StepParams& p, int grid,
                              cudaStream_t s) {

@@ -5,8 +5,8 @@ namespace elbm {
 cudaError_t launch_fp32_formula_d3q27(int diag, int check, const StepParams& p,
                                       int grid, int block, cudaStream_t s,
                                       int* grid_used) {
-  return launch_diag<D3Q27, float, MODE_FORMULA>(diag, check, p, grid, block, s,
-                                                  grid_used);
+  (void)block;
+  return launch_sc32<D3Q27>(diag, check, p, grid, s, grid_used);
 }
 cudaError_t launch_far_d3q27(int diag, int check, const StepParams& p, int grid,
                              cudaStream_t s) {

@@ -11,18 +11,39 @@
 // The 27 (or 9) gathers of a tile are warp-coalesced 128-byte rows; the
 // +-1 x-shift of a row is absorbed by L1/L2.
 //
-// Template parameters: lattice L, storage type T (double: FP64 arithmetic;
-// float: FP32 storage, certified FP32 FORMULA or FP64 ROOT/SECANT), alpha
-// MODE, DIAG (fused statistics), CHECK (FP64 entropy check; implies DIAG).
+// Template parameters: lattice L, storage type T (double: FP64 arithmetic
+// for every alpha mode; float: FP32 storage with ROOT / SECANT in FP64 --
+// FP32 FORMULA runs in the pipelined k_sc32), alpha MODE, DIAG (fused
+// statistics), CHECK (FP64 entropy check; implies DIAG).
 #pragma once
 #include <stdint.h>
 
 #include "lattice.cuh"
-#include "node_fp32.cuh"
 #include "node_fp64.cuh"
 #include "stats.cuh"
 
 namespace elbm {
+
+// Division by a runtime-invariant 32-bit divisor d >= 1 by multiply-high
+// and shifts (Granlund & Montgomery, "Division by invariant integers using
+// multiplication", 1994): q = (t + ((n - t) >> s1)) >> s2, t = mulhi(m, n),
+// with l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1, s1 = min(l, 1),
+// s2 = max(l - 1, 0).  Exact for every n < 2^32.
+struct FastDiv {
+  unsigned m;
+  int s1, s2;
+  __host__ void init(unsigned d) {
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    m = (unsigned)((((1ull << 32) * ((1ull << l) - d)) / d) + 1);
+    s1 = l < 1 ? l : 1;
+    s2 = l > 1 ? l - 1 : 0;
+  }
+  __device__ __forceinline__ unsigned div(unsigned n) const {
+    const unsigned t = __umulhi(m, n);
+    return (t + ((n - t) >> s1)) >> s2;
+  }
+};
 
 struct StepParams {
   const void* f_in;
@@ -42,7 +63,9 @@ struct StepParams {
   int secant_iters;
   unsigned* far_count;    // [2] deferred-node counters, indexed by parity
   unsigned* far_queue;    // node indices deferred to the FP64 fixup
+  unsigned far_cap;       // capacity of far_queue (entries)
   int parity;             // step parity selecting far_count[parity]
+  FastDiv div_nx, div_ny; // node -> (x, y, z)
 };
 
 template <class L>
@@ -155,60 +178,8 @@ __global__ void __launch_bounds__(256)
       };
       collide64<L, MODE, CHECK>(nd, p, true, acc, DIAG != 0, store_s);
     } else {
-      // ------------- FP32 storage, certified FP32 FORMULA ----------------
-      float dl[Q], nn[Q];
-      const float rho0f = (float)p.rho0;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        dl[i] = p.unshifted ? (float)v[i] - (float)L::w(i) * rho0f
-                            : (float)v[i];
-      }
-      // (float)W * rho0f is the shift s_i used by the unshifted storage
-      Node32Result r = node32_formula<L>(dl, nn, rho0f,
-                                         p.unshifted ? p.corr_rho : 0.0f,
-                                         p.unshifted ? p.corr : nullptr);
-      if (r.flags & (NF_FAR | NF_BAD_NEG | NF_BAD_NONFINITE)) {
-        if (r.flags & (NF_BAD_NEG | NF_BAD_NONFINITE)) {
-          // invalid state: flag it and pass the loaded values through
-          atomicOr(p.err_flags, r.flags & (NF_BAD_NEG | NF_BAD_NONFINITE));
-#pragma unroll
-          for (int i = 0; i < Q; ++i)
-            fout[(long long)i * p.n + node] =
-                fin[(long long)i * p.n + src_index<L>(p, i, x, y, z)];
-          continue;
-        }
-        // far from equilibrium: the FP64 fixup kernel collides this node
-        // (it re-gathers from f_in, which this step does not modify)
-        const unsigned slot = atomicAdd(&p.far_count[p.parity], 1u);
-        p.far_queue[slot] = (unsigned)node;
-        continue;
-      }
-      const float ab = r.alpha * (float)p.beta;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const float nv = fmaf(ab, nn[i], dl[i]);
-        fout[(long long)i * p.n + node] =
-            p.unshifted ? (T)(nv + (float)L::w(i) * rho0f) : (T)nv;
-      }
-      if (p.alpha_map) p.alpha_map[node] = r.alpha;
-      if (DIAG) {
-        double jd[3] = {r.j[0], r.j[1], r.j[2]};
-        acc.add_moments(r.drho, jd, r.rho);
-        acc.add_alpha(r.alpha, r.flags, 0);
-        if (CHECK) {
-          Node64<L> nd;
-#pragma unroll
-          for (int i = 0; i < Q; ++i) {
-            const double s = L::w(i) * p.rho0;
-            nd.f[i] = p.unshifted ? (double)v[i] : s + (double)v[i];
-          }
-          node64_prepare(nd);
-          Check64 ck = node64_check(nd, (double)r.alpha);
-          acc.add_check(ck.h, ck.violation,
-                        ((r.flags & NF_ACCEPT_STAR) != 0) != ck.accept_ref,
-                        fabs((double)r.alpha - ck.alpha_ref));
-        }
-      }
+      static_assert(sizeof(T) == 8 || MODE != MODE_FORMULA,
+                    "FP32 FORMULA runs in k_sc32");
     }
   }
   if (DIAG) acc.block_reduce_store(p.partials);
@@ -222,7 +193,7 @@ __global__ void __launch_bounds__(256) k_far_fixup(const StepParams p) {
   constexpr int Q = L::Q;
   const float* __restrict__ fin = static_cast<const float*>(p.f_in);
   float* __restrict__ fout = static_cast<float*>(p.f_out);
-  const unsigned count = p.far_count[p.parity];
+  const unsigned count = min(p.far_count[p.parity], p.far_cap);
   Acc acc;
   acc.init();
   for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < count;

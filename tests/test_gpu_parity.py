@@ -1,12 +1,13 @@
 """GPU parity of the CUDA path (through the C ABI) against the CPU oracle.
 
 Tolerances:
-  * FP64 storage, FORMULA / SECANT: every population within 1e-12 relative
-    (the two evaluate the same Eqs. (1)-(9) in FP64; differences are
-    rounding order, FMA contraction and 1-ulp log differences);
-  * FP64 ROOT: the bisection's branch sequence can differ where Delta H(mid)
-    is within rounding of 0 or -1e-13, so the single-step check is that the
-    GPU alpha satisfies the oracle's stop rule, and fields agree to 1e-9;
+  * FP64 storage, FORMULA: every population within 1e-12 relative (the two
+    evaluate the same Eqs. (1)-(9) in FP64; differences are rounding order,
+    FMA contraction and 1-ulp log differences);
+  * FP64 ROOT / SECANT: iterative branch sequences can differ where Delta H
+    is within rounding of a stop-rule edge, so fields agree to 1e-9 and the
+    single-step check is that every GPU alpha (recovered from the FP64
+    populations) satisfies the oracle's stop rule / H-inequality;
   * FP32 storage: velocity L2-relative 1e-5 against the FP64 oracle on
     laminar flows; per-node alpha never above the FP64 FORMULA alpha of the
     same stored state and within 1e-4 of it where the state is resolved
@@ -81,8 +82,7 @@ def test_fp64_taylor_green_64_1000_steps(elbm, orc):
 
 @pytest.mark.parametrize("lat,shape", [("D2Q9", (1, 23, 37)),
                                        ("D3Q27", (11, 13, 19))])
-@pytest.mark.parametrize("mode", ["formula", "secant"])
-def test_fp64_ragged_parity(elbm, orc, lat, shape, mode):
+def test_fp64_ragged_formula_parity(elbm, orc, lat, shape):
     nz, ny, nx = shape
     if lat == "D2Q9":
         rho, u = W.random_phase_2d(nx, seed=3, umax=0.1, ny=ny)
@@ -91,8 +91,8 @@ def test_fp64_ragged_parity(elbm, orc, lat, shape, mode):
     g, o = _pair(elbm, orc, lat, shape, 2e-4, "fp64", rho, u)
     g.set_diagnostics(diag_every=1, check_every=1, alpha_map_every=1)
     for _ in range(3):
-        g.step(10, mode)
-        amaps, _ = o.step(10, mode, secant_iters=4, alpha_map=True)
+        g.step(10, "formula")
+        amaps, _ = o.step(10, "formula", alpha_map=True)
         f = g.populations()
         assert np.all(np.abs(f - o.f) <= 1e-12 * np.abs(o.f)), _rel(f, o.f)
         assert np.abs(g.alpha_map() - amaps[-1]).max() < 2e-6   # FP32 map
@@ -100,37 +100,59 @@ def test_fp64_ragged_parity(elbm, orc, lat, shape, mode):
     assert s["checked"] == 1 and s["n_violations"] == 0
 
 
+def _alpha_from_step(orc, lat, f_pre, f_post, beta):
+    """alpha of every node recovered from an FP64 step: the post-collision
+    f~_i(x) = f_post_i(x + c_i) = f_i + alpha beta (f^eq_i - f_i)."""
+    c, w = orc.lattice(lat)
+    d = orc.dim(lat)
+    q = len(w)
+    ft = np.stack([np.roll(f_post[i], shift=(-c[i, 2], -c[i, 1], -c[i, 0]),
+                           axis=(0, 1, 2)) for i in range(q)])
+    fp = f_pre.reshape(q, -1)
+    ft = ft.reshape(q, -1)
+    rho = fp.sum(0)
+    alphas, xs = [], []
+    for k in range(fp.shape[1]):
+        feq = orc.equilibrium(lat, rho[k], (c[:, :d].T @ fp[:, k]) / rho[k])
+        nk = feq - fp[:, k]
+        alphas.append(float(np.dot(ft[:, k] - fp[:, k], nk) / (beta * np.dot(nk, nk))))
+        xs.append(feq / fp[:, k] - 1)
+    return np.array(alphas), xs
+
+
 @pytest.mark.parametrize("lat,shape", [("D2Q9", (1, 20, 24)),
                                        ("D3Q27", (6, 7, 9))])
-def test_fp64_root_parity(elbm, orc, lat, shape):
+@pytest.mark.parametrize("mode", ["root", "secant"])
+def test_fp64_iterative_modes_parity(elbm, orc, lat, shape, mode):
+    """ROOT / SECANT: iterative branches can differ where Delta H is within
+    rounding of a stop-rule edge, so fields agree to 1e-9 and every GPU alpha
+    satisfies the stop rule (ROOT) or the H-inequality (SECANT) when
+    re-evaluated by the oracle."""
     nz, ny, nx = shape
     if lat == "D2Q9":
         rho, u = W.random_phase_2d(nx, seed=5, umax=0.1, ny=ny)
     else:
         rho, u = W.random_phase_3d(nx, seed=5, umax=0.1, ny=ny, nz=nz)
     g, o = _pair(elbm, orc, lat, shape, 1e-4, "fp64", rho, u)
-    g.set_diagnostics(diag_every=1, check_every=1, alpha_map_every=1)
-    g.step(20, "root")
-    o.step(20, "root")
-    f = g.populations()
-    assert _rel(f, o.f) < 1e-9
-    # one more step: the GPU alpha satisfies the oracle's stop rule
-    f_pre = g.populations().reshape(len(f), -1)
-    g.step(1, "root")
-    amap = g.alpha_map().reshape(-1)
-    c, w = orc.lattice(lat)
-    d = orc.dim(lat)
-    for node in range(0, f_pre.shape[1], max(1, f_pre.shape[1] // 200)):
-        fn = f_pre[:, node]
-        rho_ = fn.sum()
-        feq = orc.equilibrium(lat, rho_, (c[:, :d].T @ fn) / rho_)
-        x = feq / fn - 1
-        a = float(amap[node])   # map is FP32; evaluate at the FP32 value
+    g.set_diagnostics(diag_every=1, check_every=1)
+    g.step(20, mode)
+    o.step(20, mode, secant_iters=4)
+    assert _rel(g.populations(), o.f) < 1e-9
+    f_pre = g.populations()
+    g.step(1, mode)
+    alphas, xs = _alpha_from_step(orc, lat, f_pre, g.populations(), g.beta)
+    fp = f_pre.reshape(len(f_pre), -1)
+    for k in range(len(alphas)):
+        if np.abs(xs[k]).max() < 1e-6:
+            continue                    # alpha not recoverable at equilibrium
+        fn, x, a = fp[:, k], xs[k], alphas[k]
         dh = orc.delta_h(fn, x, a)
-        tol = orc.delta_h_bound(fn, x, a) + abs(
-            np.sum(fn * x * (np.log1p(a * x) - np.log1p(x)))) * 1e-7
-        assert dh <= tol
-        assert dh >= -1e-13 - tol or orc.alpha_max(fn, feq) < 2.1
+        slope = abs(np.sum(fn * x * (np.log1p(a * x) - np.log1p(x))))
+        tol = orc.delta_h_bound(fn, x, a) + slope * 1e-12 * a
+        assert dh <= tol, (k, dh, tol)
+        if mode == "root":
+            feq = fn * (1 + x)
+            assert dh >= -1e-13 - tol or orc.alpha_max(fn, feq) < 2.1
     s = g.entropy_stats()
     assert s["n_violations"] == 0 and s["n_root_cap"] == 0
 
@@ -145,9 +167,14 @@ def test_fp32_taylor_green_2d_vs_fp64_oracle(elbm, orc, dtype, tol):
     o.step(1000)
     _, ug = g.moments()
     _, uo = o.moments()
-    assert np.linalg.norm(ug - uo) / np.linalg.norm(uo) < tol
+    err = np.linalg.norm(ug - uo) / np.linalg.norm(uo)
+    print("FP32 %s TGV-64 velocity L2 rel error after 1000 steps: %.3e"
+          % (dtype, err))
+    assert err < tol
+    g.set_diagnostics(diag_every=1, check_every=1)
+    g.step(1, "formula")
     s = g.entropy_stats()
-    assert s["n_violations"] == 0
+    assert s["n_violations"] == 0 and s["checked"] == 1
 
 
 def test_fp32_taylor_green_3d_vs_fp64_oracle(elbm, orc):
@@ -160,6 +187,8 @@ def test_fp32_taylor_green_3d_vs_fp64_oracle(elbm, orc):
     _, ug = g.moments()
     _, uo = o.moments()
     assert np.linalg.norm(ug - uo) / np.linalg.norm(uo) < 1e-5
+    g.set_diagnostics(diag_every=1, check_every=1)
+    g.step(1, "formula")
     s = g.entropy_stats()
     assert s["n_violations"] == 0 and s["checked"] == 1
 
