@@ -310,7 +310,7 @@ def run_elbm(args):
         },
         "roofline": {
             "bound": "hbm",
-            "kernel": "k_stream_collide<D3Q27,float,FORMULA>",
+            "kernel": "k_sc32<D3Q27,shifted> (pipelined FP32 FORMULA stream-collide)",
             "achieved": round(achieved, 1),
             "peak": hbm,
             "peak_kind": hbm_kind,

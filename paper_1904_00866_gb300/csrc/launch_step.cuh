@@ -55,10 +55,10 @@ static cudaError_t launch_fp64_modes(int mode, int diag, int check,
 }
 
 // Pipelined FP32 FORMULA kernel (dynamic shared memory: 2 stages x Q x 256).
-template <class L, int DIAG, int CHECK>
+template <class L, bool SHIFTED, int DIAG, int CHECK>
 static cudaError_t launch_sc32_one(const StepParams& p, int grid,
                                    cudaStream_t s, int* grid_used) {
-  auto k = k_sc32<L, DIAG, CHECK>;
+  auto k = k_sc32<L, SHIFTED, DIAG, CHECK>;
   const int smem = 2 * L::Q * kSc32Threads * (int)sizeof(float);
   static bool configured = false;   // per instantiation
   if (!configured) {
@@ -84,12 +84,20 @@ static cudaError_t launch_sc32_one(const StepParams& p, int grid,
   return cudaGetLastError();
 }
 
+template <class L, bool SHIFTED>
+static cudaError_t launch_sc32_s(int diag, int check, const StepParams& p,
+                                 int grid, cudaStream_t s, int* grid_used) {
+  if (check) return launch_sc32_one<L, SHIFTED, 1, 1>(p, grid, s, grid_used);
+  if (diag) return launch_sc32_one<L, SHIFTED, 1, 0>(p, grid, s, grid_used);
+  return launch_sc32_one<L, SHIFTED, 0, 0>(p, grid, s, grid_used);
+}
+
 template <class L>
 static cudaError_t launch_sc32(int diag, int check, const StepParams& p,
                                int grid, cudaStream_t s, int* grid_used) {
-  if (check) return launch_sc32_one<L, 1, 1>(p, grid, s, grid_used);
-  if (diag) return launch_sc32_one<L, 1, 0>(p, grid, s, grid_used);
-  return launch_sc32_one<L, 0, 0>(p, grid, s, grid_used);
+  if (p.unshifted)
+    return launch_sc32_s<L, false>(diag, check, p, grid, s, grid_used);
+  return launch_sc32_s<L, true>(diag, check, p, grid, s, grid_used);
 }
 
 // The fixup grid must equal the grid of the FP32 step when DIAG is set (its

@@ -15,8 +15,8 @@
 // the Taylor series of sum f [phi(alpha x) - alpha x ln(1 + x)] (the linear
 // term alpha sum f x is exactly zero).  At alpha = 2 the k = 2 coefficient
 // vanishes, so Delta H(2) carries no O(x^2) cancellation.  The series is
-// truncated after k = 5, or k = 8 when max|x_i| > 1/40; nodes with
-// max|x_i| > 1/8 are solved in FP64.
+// truncated after k = 4, or k = 8 when max|x_i| > 1/100; nodes with
+// max|x_i| > 1/8 (or invalid states) are solved in FP64.
 //
 // Every quantity has an a-priori bound on its FP32 error (unit roundoff
 // u = 2^-24):  E_x bounds |x_i - x_i exact| (equilibrium products, velocity
@@ -29,7 +29,8 @@
 //                              decreases in both values, so it stays at or
 //                              below the exact Eq. (9) value, which is at or
 //                              below the root of Eq. (4));
-//   else (node within FP32 noise of equilibrium) -> solved in FP64.
+//   else (node within FP32 noise of equilibrium) -> alpha = 1, for which
+//                              H(f*) = H(f^eq) <= H(f) holds exactly.
 // When |Delta H(2)| <= e2 the decision is flagged NF_BAND.
 #pragma once
 #include <math.h>
@@ -50,6 +51,20 @@ struct N32 {
 };
 
 __host__ __device__ constexpr int cidx(int c) { return c + 1; }
+
+// 1 / y by the SFU (rcp.approx.ftz.f32, relative error below 2^-23).
+__device__ __forceinline__ float rcp_approx(float y) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y));
+  return r;
+}
+
+// Index 0..3 of the distinct weight of population i (number of nonzero
+// velocity components).
+template <class L>
+__host__ __device__ constexpr int wclass(int i) {
+  return L::nonzero(i);
+}
 
 // Mass/momentum of delta: rho-part and the three momentum components, from
 // per-(cy, cz) column sums (53 additions for D3Q27, 14 for D2Q9).
@@ -87,12 +102,12 @@ __device__ __forceinline__ void moment_sums(Get get, float& m0, float& mx,
   mz = sz;
 }
 
-// dl(i): FP32 deviation delta_i.  corr_rho / corr: zero for shifted
-// storage; for plain FP32 storage (delta_i = v_i - s_i, s_i = fl(W_i rho0))
+// d[i]: FP32 deviation delta_i (registers).  corr_rho / corr: used only for
+// plain FP32 storage (delta_i = v_i - s_i, s_i = fl(W_i rho0)), where
 // corr_rho = sum_i s_i - rho0 and corr_i = W_i rho0 - s_i.
-template <class L, class Get>
-__device__ __forceinline__ void node32_formula(Get dl, float rho0,
-                                               float corr_rho,
+template <class L, bool SHIFTED>
+__device__ __forceinline__ void node32_formula(const float (&d)[L::Q],
+                                               float rho0, float corr_rho,
                                                const float* __restrict__ corr,
                                                float a_extra, N32<L>& r) {
   constexpr int Q = L::Q;
@@ -101,16 +116,14 @@ __device__ __forceinline__ void node32_formula(Get dl, float rho0,
   r.alpha = 2.0f;
 
   // ---- exact mass and momentum: delta = hi + lo, hi on a 2^-20 grid ------
+  float hi[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) hi[i] = (d[i] + 12.0f) - 12.0f;
   float h0, hx, hy, hz, l0, lx, ly, lz;
-  moment_sums<L>([&](int i) { return (dl(i) + 12.0f) - 12.0f; }, h0, hx, hy,
-                 hz);
-  moment_sums<L>(
-      [&](int i) {
-        const float d = dl(i);
-        return d - ((d + 12.0f) - 12.0f);
-      },
-      l0, lx, ly, lz);
-  const float drho = (h0 + l0) + corr_rho;
+  moment_sums<L>([&](int i) { return hi[i]; }, h0, hx, hy, hz);
+  moment_sums<L>([&](int i) { return d[i] - hi[i]; }, l0, lx, ly, lz);
+  float drho = h0 + l0;
+  if (!SHIFTED) drho += corr_rho;
   const float j[3] = {hx + lx, hy + ly, hz + lz};
   const float rho = rho0 + drho;
   r.drho = drho;
@@ -119,10 +132,10 @@ __device__ __forceinline__ void node32_formula(Get dl, float rho0,
   r.j[1] = j[1];
   r.j[2] = j[2];
   if (!(rho > 0.0f) || !isfinite(rho)) {
-    r.flags = NF_BAD_NONFINITE;
+    r.flags = NF_FAR;          // the FP64 fixup classifies the state
     return;
   }
-  const float inv_rho = __fdividef(1.0f, rho);
+  const float inv_rho = rcp_approx(rho);
 
   // ---- per-axis equilibrium factors -------------------------------------
   float dp[3], dm[3], d0[3];
@@ -137,7 +150,7 @@ __device__ __forceinline__ void node32_formula(Get dl, float rho0,
     d0[a] = -s;
   }
   if (!(U < 0.5f)) {
-    r.flags = (U < 1.0f) ? NF_FAR : NF_BAD_NONFINITE;
+    r.flags = NF_FAR;
     return;
   }
   // two-axis products (1 + a)(1 + b) - 1, shared by the z-columns
@@ -151,10 +164,20 @@ __device__ __forceinline__ void node32_formula(Get dl, float rho0,
       pxy[a][b] = fmaf(da, db, da + db);
     }
 
-  // ---- n_i, x_i and the moments M_2..M_5 ---------------------------------
-  float M2 = 0.f, M3 = 0.f, M4 = 0.f, M5 = 0.f;
+  // ---- n_i, x_i and the moments M_2..M_4 ---------------------------------
+  // A population f_i <= 0 gives |x_i| >= 1 (f^eq_i > 0), so invalid states
+  // leave through the far branch, where the FP64 fixup flags them.
+  // per weight class: W rho, W drho, W rho0
+  float wr[4], wd[4], w0[4];
+#pragma unroll
+  for (int k = 0; k <= L::D; ++k) {
+    const float wk = k == 0 ? L::wf(0) : L::wf(k == 1 ? 1 : (k == 2 ? 7 : 19));
+    wr[k] = wk * rho;
+    wd[k] = wk * drho;
+    w0[k] = wk * rho0;
+  }
+  float M2 = 0.f, M3 = 0.f, M4 = 0.f;
   float xabs = 0.0f;
-  bool nonpos = false;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
@@ -163,31 +186,21 @@ __device__ __forceinline__ void node32_formula(Get dl, float rho0,
       const float a2 = cz == 1 ? dp[2] : (cz == -1 ? dm[2] : d0[2]);
       pm1 = fmaf(pm1, a2, pm1 + a2);
     }
-    const float wf = L::wf(i);
-    float deq = wf * fmaf(rho, pm1, drho);
-    if (corr) deq += corr[i];
-    const float d = dl(i);
-    const float ni = deq - d;
+    const int k = wclass<L>(i);
+    float deq = fmaf(wr[k], pm1, wd[k]);      // W (drho + rho (P - 1))
+    if (!SHIFTED) deq += corr[i];
+    const float ni = deq - d[i];
     r.n[i] = ni;
-    const float fi = fmaf(wf, rho0, d);
-    nonpos |= !(fi > 0.0f);
-    const float x = __fdividef(ni, fi);
+    const float x = ni * rcp_approx(w0[k] + d[i]);
     xabs = fmaxf(xabs, fabsf(x));
-    float p = ni * x;
-    M2 += p;
-    p *= x;
-    M3 += p;
-    p *= x;
-    M4 += p;
-    p *= x;
-    M5 += p;
+    const float q1 = ni * x;                   // f x^2
+    M2 += q1;
+    const float q2 = q1 * x;                   // f x^3
+    M3 += q2;
+    M4 = fmaf(q2, x, M4);                      // f x^4
   }
-  if (nonpos) {
-    r.flags = NF_BAD_NEG;
-    return;
-  }
-  if (!(xabs <= 0.125f)) {   // includes NaN
-    r.flags = isfinite(xabs) ? NF_FAR : NF_BAD_NONFINITE;
+  if (!(xabs <= 0.125f)) {   // far from equilibrium, invalid, or NaN
+    r.flags = NF_FAR;
     return;
   }
   if (xabs == 0.0f) {        // f^eq == f in FP32
@@ -195,15 +208,16 @@ __device__ __forceinline__ void node32_formula(Get dl, float rho0,
     return;
   }
   // longer series for nodes further from equilibrium
-  const bool k8 = xabs > 0.025f;
-  float M6 = 0.f, M7 = 0.f, M8 = 0.f;
+  const bool k8 = xabs > 0.01f;
+  float M5 = 0.f, M6 = 0.f, M7 = 0.f, M8 = 0.f;
   if (k8) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const float d = dl(i);
-      const float x = __fdividef(r.n[i], fmaf(L::wf(i), rho0, d));
+      const float x = r.n[i] * rcp_approx(w0[wclass<L>(i)] + d[i]);
       const float x2 = x * x;
-      float p = r.n[i] * x2 * x2 * x;   // n x^5 = f x^6
+      float p = r.n[i] * x2 * x2;   // n x^4 = f x^5
+      M5 += p;
+      p *= x;
       M6 += p;
       p *= x;
       M7 += p;
@@ -230,34 +244,35 @@ __device__ __forceinline__ void node32_formula(Get dl, float rho0,
   // c_k(alpha) = (-1)^k (alpha^k - k alpha) / (k (k-1))
   // c(2): k=3..8: -1/3, 2/3, -11/10, 26/15, -19/7, 30/7
   // c(1): k=2..8: -1/2, 1/3, -1/4, 1/5, -1/6, 1/7, -1/8
-  float D2 = fmaf(-1.0f / 3.0f, M3, fmaf(2.0f / 3.0f, M4, -1.1f * M5));
-  float D1 = fmaf(-0.5f, M2,
-                  fmaf(1.0f / 3.0f, M3, fmaf(-0.25f, M4, 0.2f * M5)));
+  float D2 = fmaf(-1.0f / 3.0f, M3, (2.0f / 3.0f) * M4);
+  float D1 = fmaf(-0.5f, M2, fmaf(1.0f / 3.0f, M3, -0.25f * M4));
   float tr2, tr1, rnd;
   const float r2 = 2.0f * xabs;
   if (k8) {
-    D2 = fmaf(26.0f / 15.0f, M6, fmaf(-19.0f / 7.0f, M7,
-                                      fmaf(30.0f / 7.0f, M8, D2)));
-    D1 = fmaf(-1.0f / 6.0f, M6, fmaf(1.0f / 7.0f, M7, fmaf(-0.125f, M8, D1)));
+    D2 = fmaf(-1.1f, M5, fmaf(26.0f / 15.0f, M6, fmaf(-19.0f / 7.0f, M7,
+                                                  fmaf(30.0f / 7.0f, M8, D2))));
+    D1 = fmaf(0.2f, M5, fmaf(-1.0f / 6.0f, M6,
+                             fmaf(1.0f / 7.0f, M7, fmaf(-0.125f, M8, D1))));
     const float r2_7 = r2 * r2 * r2 * r2 * r2 * r2 * r2;
     const float x7 = xabs * xabs * xabs * xabs * xabs * xabs * xabs;
+    // tails sum_{k>=9}: |c_k(2)| <= 2^k / (k (k-1)), |c_k(1)| = 1 / k,
+    // |M_k| <= xabs^(k-2) M_2
     tr2 = r2_7 / (18.0f * (1.0f - r2));
     tr1 = x7 / (9.0f * (1.0f - xabs));
-    rnd = fabsf(M6) * 1.74f + fabsf(M7) * 2.72f + fabsf(M8) * 4.29f;
+    rnd = fabsf(M5) * 1.1f + fabsf(M6) * 1.74f + fabsf(M7) * 2.72f +
+          fabsf(M8) * 4.29f;
   } else {
-    const float r2_4 = r2 * r2 * r2 * r2;
-    const float x4 = xabs * xabs * xabs * xabs;
-    tr2 = r2_4 * (2.0f / 15.0f) / (1.0f - r2);
-    tr1 = x4 / (6.0f * (1.0f - xabs));
+    // tails sum_{k>=5}
+    const float r2_3 = r2 * r2 * r2;
+    tr2 = r2_3 * 0.2f / (1.0f - r2);
+    tr1 = xabs * xabs * xabs / (5.0f * (1.0f - xabs));
     rnd = 0.0f;
   }
   const float e2 =
       M2 * (2.02f * Ex +
             gq * xabs * (0.34f + xabs * (0.7f + xabs * (1.2f + 1.8f * xabs))) +
             tr2) +
-      4.0f * uu *
-          (fabsf(M3) * (1.0f / 3.0f) + fabsf(M4) * (2.0f / 3.0f) +
-           fabsf(M5) * 1.1f + rnd) +
+      4.0f * uu * (fabsf(M3) * (1.0f / 3.0f) + fabsf(M4) * (2.0f / 3.0f) + rnd) +
       2.0f * rho * (xabs + Ex) * Ex * Ex;
   const float S1b = sqrtf(rho * M2);   // >= sum f |x|  (Cauchy-Schwarz)
   const float e1 = 1.01f * Ex * S1b / (1.0f - xabs) +
@@ -271,14 +286,21 @@ __device__ __forceinline__ void node32_formula(Get dl, float rho0,
     return;
   }
   const float D1hi = __fadd_ru(D1, e1);
-  if (!(D1hi < 0.0f)) {      // within FP32 noise of equilibrium
-    r.flags = NF_FAR;
+  if (!(D1hi < 0.0f)) {
+    // Within FP32 noise of equilibrium: neither sign is certified, but
+    // alpha = 1 (f* = f^eq) satisfies H(f*) <= H(f) exactly.  Here n is at
+    // the level of the FP32 error of the equilibrium, so the relaxation
+    // rate it implies is immaterial.
+    r.flags = NF_FORMULA | NF_BAND;
+    r.alpha = 1.0f;
     return;
   }
   const bool band = __fsub_rd(D2, e2) <= 0.0f;
   // alpha = 2 + D2hi / (D2hi - D1hi) (1 - 2), rounded down
+  // t = D2hi / (D2hi - D1hi) rounded up: the approximate quotient (error
+  // <= 2 ulp) is raised by 4 ulp
   const float den = __fsub_rd(D2hi, D1hi);
-  const float tt = __fdiv_ru(D2hi, den);
+  const float tt = __fmul_ru(__fdividef(D2hi, den), 1.0f + 2.384185791e-7f);
   r.alpha = __fsub_rd(2.0f, tt);
   r.flags = NF_FORMULA | (band ? NF_BAND : 0u);
 }

@@ -646,6 +646,12 @@ elbm_status elbm_step(elbm_handle* h, long long nsteps, elbm_alpha_mode mode) {
     const bool amap = h->amap_every > 0 && n % h->amap_every == 0;
     p.f_in = h->f[h->cur];
     p.f_out = h->f[h->cur ^ 1];
+    if (storage == 1) {
+      for (int i = 0; i < h->q; ++i) {
+        p.in_pop[i] = (const float*)p.f_in + (size_t)i * h->n;
+        p.out_pop[i] = (float*)p.f_out + (size_t)i * h->n;
+      }
+    }
     p.alpha_map = amap ? h->alpha_map : nullptr;
     p.parity = (int)(n & 1);
     int grid = 0;

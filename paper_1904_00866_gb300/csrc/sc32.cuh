@@ -75,9 +75,8 @@ __device__ __forceinline__ void node_xyz(const StepParams& p, unsigned node,
 }
 
 template <class L>
-__device__ __forceinline__ void issue_tile(const StepParams& p,
-                                           const float* __restrict__ fin,
-                                           float* sm, unsigned tile) {
+__device__ __forceinline__ void issue_tile(const StepParams& p, float* sm,
+                                           unsigned tile) {
   const unsigned node = tile * kSc32Threads + threadIdx.x;
   if (node >= (unsigned)p.n) return;
   int x, y, z;
@@ -94,33 +93,29 @@ __device__ __forceinline__ void issue_tile(const StepParams& p,
     const int zs = cz == 1 ? zm : (cz == -1 ? zp : z);
     const unsigned off = ((unsigned)zs * (unsigned)p.ny + (unsigned)ys) *
                              (unsigned)p.nx + (unsigned)xs;
-    cp_async4(sm + i * kSc32Threads + threadIdx.x,
-              fin + (size_t)i * (size_t)p.n + off);
+    cp_async4(sm + i * kSc32Threads + threadIdx.x, p.in_pop[i] + off);
   }
 }
 
-template <class L, int DIAG, int CHECK>
+template <class L, bool SHIFTED, int DIAG, int CHECK>
 __global__ void __launch_bounds__(kSc32Threads, 2)
     k_sc32(const StepParams p) {
   constexpr int Q = L::Q;
   extern __shared__ float smem[];   // [2][Q][256]
-  const float* __restrict__ fin = static_cast<const float*>(p.f_in);
-  float* __restrict__ fout = static_cast<float*>(p.f_out);
   const unsigned ntiles = (unsigned)((p.n + kSc32Threads - 1) / kSc32Threads);
   const float rho0f = (float)p.rho0;
   const float beta = (float)p.beta;
-  const bool unshifted = p.unshifted != 0;
   Acc32 acc;
   if (DIAG) acc.init();
 
   unsigned tile = blockIdx.x;
   int stage = 0;
-  if (tile < ntiles) issue_tile<L>(p, fin, smem, tile);
+  if (tile < ntiles) issue_tile<L>(p, smem, tile);
   cp_async_commit();
   for (; tile < ntiles; tile += gridDim.x) {
     const unsigned next = tile + gridDim.x;
     if (next < ntiles)
-      issue_tile<L>(p, fin, smem + (stage ^ 1) * Q * kSc32Threads, next);
+      issue_tile<L>(p, smem + (stage ^ 1) * Q * kSc32Threads, next);
     cp_async_commit();
     cp_async_wait<1>();   // this thread's copies of `tile` have landed
 
@@ -129,44 +124,37 @@ __global__ void __launch_bounds__(kSc32Threads, 2)
     stage ^= 1;
     if (node >= (unsigned)p.n) continue;
 
-    auto dl = [&](int i) -> float {
+    float d[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
       const float v = sm[i * kSc32Threads];
-      return unshifted ? v - L::wf(i) * rho0f : v;
-    };
+      d[i] = SHIFTED ? v : v - L::wf(i) * rho0f;
+    }
     float a_extra = 0.0f;
-    if (unshifted) {
+    if (!SHIFTED) {
       // delta_i = v_i - s_i is exact unless v_i leaves [s_i/2, 2 s_i]
       float A = 0.0f;
 #pragma unroll
-      for (int i = 0; i < Q; ++i) A += fabsf(dl(i));
+      for (int i = 0; i < Q; ++i) A += fabsf(d[i]);
       a_extra = 2.0f * 5.9604645e-8f * A / rho0f;
     }
     N32<L> r;
-    node32_formula<L>(dl, rho0f, unshifted ? p.corr_rho : 0.0f,
-                      unshifted ? p.corr : nullptr, a_extra, r);
-    if (r.flags & (NF_FAR | NF_BAD_NEG | NF_BAD_NONFINITE)) {
-      if (r.flags & (NF_BAD_NEG | NF_BAD_NONFINITE)) {
-        // invalid state: flag it and pass the loaded values through
-        atomicOr(p.err_flags, r.flags & (NF_BAD_NEG | NF_BAD_NONFINITE));
-#pragma unroll
-        for (int i = 0; i < Q; ++i)
-          fout[(size_t)i * p.n + node] = sm[i * kSc32Threads];
-      } else {
-        // far from (or within FP32 noise of) equilibrium: FP64 fixup
-        const unsigned slot = atomicAdd(&p.far_count[p.parity], 1u);
-        if (slot < p.far_cap)
-          p.far_queue[slot] = node;
-        else
-          atomicOr(p.err_flags, NF_BAD_NONFINITE);   // cannot happen: cap = n
-      }
+    node32_formula<L, SHIFTED>(d, rho0f, p.corr_rho, p.corr, a_extra, r);
+    if (r.flags & NF_FAR) {
+      // far from (or invalid, or within FP32 noise of) equilibrium: the FP64
+      // fixup collides this node from f_in
+      const unsigned slot = atomicAdd(&p.far_count[p.parity], 1u);
+      if (slot < p.far_cap)
+        p.far_queue[slot] = node;
+      else
+        atomicOr(p.err_flags, NF_BAD_NONFINITE);   // cannot happen: cap = n
       continue;
     }
     // relax with the conservation-projected n:  f~ = f + alpha beta n
     const float ab = r.alpha * beta;
     projection<L>(r.n, [&](int i, float wt) {
-      const float d = dl(i);
-      const float nv = fmaf(ab, r.n[i] - wt, d);
-      fout[(size_t)i * p.n + node] = unshifted ? nv + L::wf(i) * rho0f : nv;
+      const float nv = fmaf(ab, r.n[i] - wt, d[i]);
+      p.out_pop[i][node] = SHIFTED ? nv : nv + L::wf(i) * rho0f;
     });
     if (p.alpha_map) p.alpha_map[node] = r.alpha;
     if (DIAG) {
@@ -189,7 +177,7 @@ __global__ void __launch_bounds__(kSc32Threads, 2)
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
           const double v = (double)sm[i * kSc32Threads];
-          nd.f[i] = unshifted ? v : L::w(i) * p.rho0 + v;
+          nd.f[i] = SHIFTED ? L::w(i) * p.rho0 + v : v;
         }
         node64_prepare(nd);
         Check64 ck = node64_check(nd, (double)r.alpha);

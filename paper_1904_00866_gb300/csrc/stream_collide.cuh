@@ -66,6 +66,8 @@ struct StepParams {
   unsigned far_cap;       // capacity of far_queue (entries)
   int parity;             // step parity selecting far_count[parity]
   FastDiv div_nx, div_ny; // node -> (x, y, z)
+  const float* in_pop[27];  // FP32 storage: f_in + i n, per population
+  float* out_pop[27];       // FP32 storage: f_out + i n
 };
 
 template <class L>

@@ -216,8 +216,21 @@ def test_fp32_single_step_alpha_against_fp64(elbm, orc, lat, shape, nu):
     ag = g.alpha_map().astype(np.float64)
     ao = amaps[0]
     assert np.all(ag <= ao + 1e-12)
+    # nodes whose non-equilibrium part is resolved in FP32 (rms x > 1e-5)
+    # follow the FP64 alpha to 1e-4; nodes within FP32 noise of equilibrium
+    # may take the certified alpha = 1
+    lf = loaded.reshape(len(loaded), -1)
+    c, w = orc.lattice(lat)
+    d = orc.dim(lat)
+    rho_ = lf.sum(0)
+    rms = np.empty(lf.shape[1])
+    for k in range(lf.shape[1]):
+        feq = orc.equilibrium(lat, rho_[k], (c[:, :d].T @ lf[:, k]) / rho_[k])
+        rms[k] = np.sqrt(np.mean((feq / lf[:, k] - 1) ** 2))
+    resolved = rms.reshape(ag.shape) > 1e-5
     close = (ao - ag) <= 1e-4
-    assert close.mean() >= 0.999, close.mean()
+    assert close[resolved].mean() >= 0.999, close[resolved].mean()
+    assert np.all((ag[~resolved] == 1.0) | close[~resolved])
     s = g.entropy_stats()
     assert s["n_violations"] == 0 and s["checked"] == 1
     assert s["n_decision_mismatch"] <= s["n_band"]
