@@ -224,6 +224,46 @@ ELBM_API elbm_status elbm_set_profiling(elbm_handle *h, int enable);
 ELBM_API elbm_status elbm_profile(elbm_handle *h, double *stream_collide_ms,
                                   long long *launches);
 
+/* One FP32-shifted FORMULA step that allocates no device memory.
+ *
+ * The paper has no counterpart: this is a deployment variant of elbm_step
+ * for callers that cannot call cudaMalloc -- an application that reserves
+ * its whole device-memory budget in its own pool at start-up and passes the
+ * library only buffers from that pool, or a latency-critical loop that must
+ * not pay for the allocator's implicit device synchronisation.
+ *
+ * f_in_device / f_out_device: caller-owned device buffers of Q * nx*ny*nz
+ * floats (distinct), in the library's FP32-shifted pull layout: population i
+ * of node x is stored at [i][x - c_i] as f~_i - W_i rho0 (the post-collision
+ * value of the previous step; the same layout elbm_step keeps internally).
+ * The step reads f_in and writes f_out.  alpha_out_device (nullable,
+ * nx*ny*nz floats) receives the per-node alpha.  rho0 is the shift's
+ * reference density (rounded to FP32).  cuda_stream: the stream to run on.
+ * stats_out (nullable, host): when given, the call computes the fused
+ * diagnostics of the step, synchronises the stream, fills *stats_out (step
+ * 0, FP64 check not evaluated) and reports flagged invalid states
+ * (ELBM_ENEGATIVE / ELBM_ENONFINITE); without it the call returns right
+ * after queueing the kernels.
+ *
+ * Limits and sharing: the kernels' scratch (deferred-node queue, diagnostic
+ * rows, statistics, counters) is one fixed ~9.1 MB __device__ array inside
+ * the library, held by every GPU that loads it until the process exits;
+ * lattices above 2,097,152 nodes are rejected with ELBM_EINVAL.  Every call
+ * uses the same array and clears its counters first, so calls whose work
+ * overlaps on the GPU (other streams, other threads) race and must be
+ * serialised by the caller.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  Errors: ELBM_EINVAL for invalid arguments or
+ * sizes, ELBM_ECUDA for CUDA errors; the message is elbm_last_error(NULL).
+ * No cudaMalloc, cudaFree or allocating library call is made. */
+ELBM_API elbm_status elbm_step_static(elbm_lattice lattice, int nx, int ny,
+                                      int nz, double nu, double rho0,
+                                      const float *f_in_device,
+                                      float *f_out_device,
+                                      float *alpha_out_device,
+                                      void *cuda_stream,
+                                      elbm_entropy_stats_t *stats_out);
+
 /* Reference density rho0 of the shifted storage (meaningful after init). */
 ELBM_API double elbm_rho0(const elbm_handle *h);
 

@@ -114,6 +114,11 @@ SIGNATURES = {
     "elbm_device_bytes": (ctypes.c_size_t, [_P]),
     "elbm_launch_count": (ctypes.c_longlong, []),
     "elbm_rho0": (ctypes.c_double, [_P]),
+    "elbm_step_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_double, ctypes.c_double, _P,
+                                        _P, _P, _P,
+                                        ctypes.POINTER(EntropyStats)]),
     "elbm_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
     "elbm_profile": (ctypes.c_int, [_P, _DP, _LLP]),
 }

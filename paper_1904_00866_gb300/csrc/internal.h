@@ -2,12 +2,25 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <string>
+
 #include "stream_collide.cuh"
 
 namespace elbm {
 
 // Launch counter shared by all launch sites.
 void count_launch();
+
+// Message returned by elbm_last_error(NULL) (thread-local).
+void set_global_error(const std::string& msg);
+
+// Sum `rows` partial rows (NSTAT doubles each) into out[NSTAT].
+cudaError_t launch_finish(const double* partials, int rows, double* out,
+                          cudaStream_t s);
+
+// Public statistics record from the NSTAT reduced slots.
+void stats_from_slots(const double* slots, double rho0, long long n,
+                      long long step, int checked, void* out_stats);
 
 // Per-translation-unit launchers.  grid <= 0 picks the occupancy-sized grid
 // (SM count x resident blocks, capped by the work); *grid_used receives it.

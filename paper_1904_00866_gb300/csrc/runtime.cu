@@ -222,6 +222,43 @@ __global__ void k_partial_sum(const double* __restrict__ x, long long n,
   if (threadIdx.x == 0) partials[blockIdx.x] = sm[0];
 }
 
+cudaError_t launch_finish(const double* partials, int rows, double* out,
+                          cudaStream_t s) {
+  k_finish<<<NSTAT, 256, 0, s>>>(partials, rows, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+void stats_from_slots(const double* s, double rho0, long long n,
+                      long long step, int checked, void* out_stats) {
+  elbm_entropy_stats_t* out = static_cast<elbm_entropy_stats_t*>(out_stats);
+  memset(out, 0, sizeof(*out));
+  out->step = step;
+  out->n_nodes = (long long)s[S_NODES];
+  out->mass = s[S_DRHO] + rho0 * (double)n;
+  out->momentum[0] = s[S_J0];
+  out->momentum[1] = s[S_J1];
+  out->momentum[2] = s[S_J2];
+  out->kinetic_energy = s[S_KE];
+  out->alpha_min = s[S_AMIN];
+  out->alpha_max = s[S_AMAX];
+  out->alpha_sum = s[S_ASUM];
+  out->n_accept_two = (long long)s[S_ACC2];
+  out->n_accept_star = (long long)s[S_ACCSTAR];
+  out->n_formula = (long long)s[S_FORMULA];
+  out->n_band = (long long)s[S_BAND];
+  out->n_far = (long long)s[S_FAR];
+  out->n_degenerate = (long long)s[S_DEGEN];
+  out->n_root_iters = (long long)s[S_ITERS];
+  out->n_root_cap = (long long)s[S_CAP];
+  out->n_no_root = (long long)s[S_NOROOT];
+  out->checked = checked;
+  out->h_total = s[S_H];
+  out->n_violations = (long long)s[S_VIOL];
+  out->n_decision_mismatch = (long long)s[S_MISMATCH];
+  out->alpha_dev_max = s[S_ADEV];
+}
+
 }  // namespace elbm
 
 using namespace elbm;
@@ -265,6 +302,10 @@ struct elbm_handle {
 };
 
 static thread_local std::string g_create_err;
+
+namespace elbm {
+void set_global_error(const std::string& msg) { g_create_err = msg; }
+}  // namespace elbm
 
 static size_t elem_size(elbm_dtype t) { return t == ELBM_FP64 ? 8 : 4; }
 
@@ -693,8 +734,7 @@ elbm_status elbm_step(elbm_handle* h, long long nsteps, elbm_alpha_mode mode) {
       rows += fgrid;
     }
     if (diag) {
-      k_finish<<<NSTAT, 256, 0, h->stream>>>(h->partials, rows, h->stats_dev);
-      count_launch();
+      launch_finish(h->partials, rows, h->stats_dev, h->stream);
       h->stats_valid = true;
       h->stats_step = n;
       h->stats_checked = check;
@@ -805,32 +845,8 @@ elbm_status elbm_entropy_stats(elbm_handle* h, elbm_entropy_stats_t* out) {
   double s[NSTAT];
   cudaError_t e = cudaMemcpy(s, h->stats_dev, sizeof(s), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(h, e, "copy stats");
-  memset(out, 0, sizeof(*out));
-  const double rho0 = h->dtype == ELBM_FP64 ? 0.0 : h->rho0;
-  out->step = h->stats_step;
-  out->n_nodes = (long long)s[S_NODES];
-  out->mass = s[S_DRHO] + rho0 * (double)h->n;
-  out->momentum[0] = s[S_J0];
-  out->momentum[1] = s[S_J1];
-  out->momentum[2] = s[S_J2];
-  out->kinetic_energy = s[S_KE];
-  out->alpha_min = s[S_AMIN];
-  out->alpha_max = s[S_AMAX];
-  out->alpha_sum = s[S_ASUM];
-  out->n_accept_two = (long long)s[S_ACC2];
-  out->n_accept_star = (long long)s[S_ACCSTAR];
-  out->n_formula = (long long)s[S_FORMULA];
-  out->n_band = (long long)s[S_BAND];
-  out->n_far = (long long)s[S_FAR];
-  out->n_degenerate = (long long)s[S_DEGEN];
-  out->n_root_iters = (long long)s[S_ITERS];
-  out->n_root_cap = (long long)s[S_CAP];
-  out->n_no_root = (long long)s[S_NOROOT];
-  out->checked = h->stats_checked;
-  out->h_total = s[S_H];
-  out->n_violations = (long long)s[S_VIOL];
-  out->n_decision_mismatch = (long long)s[S_MISMATCH];
-  out->alpha_dev_max = s[S_ADEV];
+  stats_from_slots(s, h->dtype == ELBM_FP64 ? 0.0 : h->rho0, h->n,
+                   h->stats_step, h->stats_checked, out);
   return ELBM_OK;
 }
 
