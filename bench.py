@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=100)
     return ap.parse_args()
 
 
@@ -226,6 +229,77 @@ def secondary(elbm, stream):
     return out
 
 
+def batched(elbm, steps=48):
+    """The 64-lattice mixed batch (half D2Q9 64..1024^2, half D3Q27
+    32..192^3, nu log-uniform in [1e-5, 1e-2], random-phase low-mode flow):
+    one persistent launch per step, graph-replayed bursts, autotuned launch
+    shape.  MLUPS over all members, device-timed."""
+    import torch
+    import elbm_workloads as W
+    specs = W.batch_specs()
+    b = elbm.Batch(burst=16, use_graphs=True, autotune=True)
+    nodes = 0
+    for sp in specs:
+        n = sp["n"]
+        nz = n if sp["lattice"] == "D3Q27" else 1
+        rho, u = W.fields_for(sp["lattice"], n, sp["seed"])
+        b.add(sp["lattice"], n, n, nz, sp["nu"], rho, u)
+        nodes += n * n * nz
+    b.step(16)        # tuning + graph capture + warm-up
+    b.sync()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = elbm.launch_count()
+    e0.record(stream)
+    b.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    out = {"members": len(specs), "nodes": nodes, "steps": steps,
+           "mlups": round(nodes * steps / (ms * 1e3), 1),
+           "gpu_launches": elbm.launch_count() - l0,
+           "tuning": b.tuning(), "device_gb": round(b.device_bytes / 1e9, 2)}
+    b.close()
+    return out
+
+
+def serving(elbm, n_requests):
+    """The first n_requests of the Poisson request stream (mean 50/s),
+    served by continuous batching within a 150 GB budget, then the same
+    requests one after another on the single-lattice path.  Initial fields
+    are generated before the clock starts (a client would send them)."""
+    import elbm_workloads as W
+    from paper_1904_00866_gb300 import serve
+    reqs = W.request_stream()[:n_requests]
+    cache = {}
+    for r in reqs:
+        cache[(r["lattice"], r["n"], r["seed"])] = W.fields_for(
+            r["lattice"], r["n"], r["seed"])
+    fields = lambda lat, n, seed: cache[(lat, n, seed)]
+    srv = serve.Server(elbm.Batch(burst=16), fields, budget_bytes=150e9,
+                       max_members=64, burst=16)
+    for r in reqs:
+        srv.submit(r)
+    rep = srv.run()
+
+    def make(req):
+        n = req["n"]
+        nz = n if req["lattice"] == "D3Q27" else 1
+        return elbm.Lattice(req["lattice"], n, n, nz, nu=req["nu"],
+                            dtype="fp32_shifted")
+    _, seq = serve.run_sequential(reqs, make, fields)
+    work = sum(serve.request_nodes(r) * r["steps"] for r in reqs)
+    span = max(r["arrival"] for r in reqs) - min(r["arrival"] for r in reqs)
+    for d in (rep, seq):
+        for k in list(d):
+            if isinstance(d[k], float):
+                d[k] = round(d[k], 4)
+    return {"requests": n_requests, "arrival_rate_per_s": 50.0,
+            "offered_mlups": round(work / max(span, 1e-9) / 1e6, 1),
+            "continuous_batching": rep, "sequential": seq}
+
+
 def cpu_baseline(target_s=12.0):
     """The CPU FP64 oracle, as it stands, on a bounded D3Q27 TGV sample."""
     import oracle
@@ -337,6 +411,10 @@ def run_elbm(args):
         result["e2e"] = e2e(elbm, args, n, nu, stream, world)
     if not args.no_secondary and rank == 0:
         result["secondary"] = secondary(elbm, stream)
+    if not args.no_batch and rank == 0:
+        result["batched"] = batched(elbm)
+    if not args.no_serve and rank == 0:
+        result["serving"] = serving(elbm, args.serve_requests)
     if not args.no_cpu and rank == 0 and world == 1:
         result["cpu_baseline"] = cpu_baseline()
     if rank == 0:

@@ -179,11 +179,52 @@ def request_stream(seed=20190402, count=2000, rate=50.0, min_steps=100,
     return reqs
 
 
+def abc_flow_3d(n, seed, umax=0.05, kmax=4):
+    """Random-phase low-mode 3D flow built from separable terms (an
+    Arnold-Beltrami-Childress flow with random amplitudes, phases and mode
+    numbers 1..kmax per term): divergence-free, max |u| rescaled to umax,
+    rho = 1.  Fast for large lattices (only 1D trigonometric factors)."""
+    rng = np.random.default_rng(seed)
+    A, B, C = rng.uniform(0.5, 1.5, size=3)
+    ka, kb, kc = rng.integers(1, kmax + 1, size=3)
+    pa, pb, pc = rng.uniform(0, 2 * math.pi, size=3)
+    t = 2 * math.pi * np.arange(n, dtype=np.float64) / n
+    X, Y, Z = t[None, None, :], t[None, :, None], t[:, None, None]
+    u = np.empty((3, n, n, n))
+    # u = A sin(k z) + C cos(k y), v = B sin(k x) + A cos(k z),
+    # w = C sin(k y) + B cos(k x): each term depends on the other two axes
+    u[0] = A * np.sin(ka * Z + pa) + C * np.cos(kc * Y + pc)
+    u[1] = B * np.sin(kb * X + pb) + A * np.cos(ka * Z + pa)
+    u[2] = C * np.sin(kc * Y + pc) + B * np.cos(kb * X + pb)
+    m = np.sqrt((u ** 2).sum(0)).max()
+    u *= umax / m
+    return np.ones((n, n, n)), u
+
+
+def shear_waves_2d(n, seed, umax=0.05, kmax=4):
+    """Random-phase low-mode 2D flow from separable shear waves,
+    u_x = a sin(k1 y + p1) + c cos(k3 y + p3), u_y = b sin(k2 x + p2)
+    (divergence-free), max |u| rescaled to umax, rho = 1."""
+    rng = np.random.default_rng(seed)
+    a, b, c = rng.uniform(0.5, 1.5, size=3)
+    k1, k2, k3 = rng.integers(1, kmax + 1, size=3)
+    p1, p2, p3 = rng.uniform(0, 2 * math.pi, size=3)
+    t = 2 * math.pi * np.arange(n, dtype=np.float64) / n
+    X, Y = t[None, :], t[:, None]
+    u = np.empty((2, 1, n, n))
+    u[0, 0] = a * np.sin(k1 * Y + p1) + c * np.cos(k3 * Y + p3) + 0.0 * X
+    u[1, 0] = b * np.sin(k2 * X + p2) + 0.0 * Y
+    m = np.sqrt((u ** 2).sum(0)).max()
+    u *= umax / m
+    return np.ones((1, n, n)), u
+
+
 def fields_for(lattice, n, seed, umax=0.05):
-    """Random-phase initial fields for one request/batch entry."""
+    """Initial fields for one batched / served lattice: random-phase
+    low-mode divergence-free flow, max |u| = umax, rho = 1."""
     if lattice == "D2Q9":
-        return random_phase_2d(n, seed, umax=umax)
-    return random_phase_3d(n, seed, umax=umax)
+        return shear_waves_2d(n, seed, umax=umax)
+    return abc_flow_3d(n, seed, umax=umax)
 
 
 def random_multipliers(rng, q, amp):

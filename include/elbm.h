@@ -264,6 +264,79 @@ ELBM_API elbm_status elbm_step_static(elbm_lattice lattice, int nx, int ny,
                                       void *cuda_stream,
                                       elbm_entropy_stats_t *stats_out);
 
+/* ------------------------------------------------------------------------
+ * Batched stepping of many independent lattices: up to 256 periodic
+ * lattices of mixed type, size and viscosity advanced together.  Every member uses FP32-shifted storage and
+ * FORMULA alpha; one persistent launch per step covers the tiles of all
+ * members (the same per-node arithmetic as elbm_step), and bursts of steps
+ * are replayed from a captured CUDA graph.  Block size and blocks per SM are
+ * chosen by an autotuner (timed dry steps, cached per membership signature;
+ * ELBM_AUTOTUNE_CACHE names an optional JSON-lines cache file).
+ * ------------------------------------------------------------------------ */
+typedef struct elbm_batch elbm_batch;
+
+typedef struct {
+  elbm_lattice lattice;
+  int nx, ny, nz;      /* nz = 1 for D2Q9 */
+  double nu;           /* > 0; beta from Eq. (2) */
+} elbm_member_spec;
+
+/* Empty batch of at most max_members (1..256) members. */
+ELBM_API elbm_status elbm_batch_create(elbm_batch **out, int max_members);
+ELBM_API void elbm_batch_destroy(elbm_batch *b);
+ELBM_API const char *elbm_batch_last_error(const elbm_batch *b);
+ELBM_API elbm_status elbm_batch_set_stream(elbm_batch *b, void *cuda_stream);
+/* Device memory callbacks for every buffer of the batch (before the first
+ * member is added). */
+ELBM_API elbm_status elbm_batch_set_allocator(
+    elbm_batch *b, void *(*alloc)(size_t bytes, void *ctx),
+    void (*free_fn)(void *ptr, void *ctx), void *ctx);
+/* diag_every: fused statistics on each member's last step of every
+ * diag_every-th burst (0: never); burst: steps per burst (1..4096, graph
+ * length); use_graphs / autotune: 0 or 1.  Defaults 0, 16, 1, 1. */
+ELBM_API elbm_status elbm_batch_set_options(elbm_batch *b, int diag_every,
+                                            int burst, int use_graphs,
+                                            int autotune);
+/* Add a member initialised to f^eq(rho, u) (host FP64 fields, layouts as
+ * elbm_init_fields).  Allocates its two population buffers.  *id_out is the
+ * member's id (slot), valid until elbm_batch_remove. */
+ELBM_API elbm_status elbm_batch_add(elbm_batch *b, const elbm_member_spec *spec,
+                                    const double *rho, const double *u,
+                                    int *id_out);
+/* Remove a member and free its buffers (synchronises the stream). */
+ELBM_API elbm_status elbm_batch_remove(elbm_batch *b, int id);
+/* Limit a member to `remaining` more steps (default: unlimited); a member
+ * with none left is frozen (not stepped) by later elbm_batch_step calls. */
+ELBM_API elbm_status elbm_batch_set_steps(elbm_batch *b, int id,
+                                          long long remaining);
+ELBM_API elbm_status elbm_batch_member_info(elbm_batch *b, int id,
+                                            long long *steps_done,
+                                            long long *remaining);
+/* Record the per-node alpha of the member's steps (0 / 1). */
+ELBM_API elbm_status elbm_batch_record_alpha(elbm_batch *b, int id, int enable);
+/* Advance every member with steps left by up to nsteps steps (each member
+ * stops when its remaining count reaches zero).  Asynchronous except on
+ * statistics bursts. */
+ELBM_API elbm_status elbm_batch_step(elbm_batch *b, long long nsteps);
+/* Synchronise; report flagged invalid states. */
+ELBM_API elbm_status elbm_batch_sync(elbm_batch *b);
+/* Readouts of one member (host buffers, layouts as the single-lattice
+ * calls).  Synchronise. */
+ELBM_API elbm_status elbm_batch_moments(elbm_batch *b, int id, double *rho_out,
+                                        double *u_out);
+ELBM_API elbm_status elbm_batch_get_populations(elbm_batch *b, int id,
+                                                double *f_out);
+ELBM_API elbm_status elbm_batch_alpha_map(elbm_batch *b, int id,
+                                          float *alpha_out);
+/* Statistics of the member's last statistics step (FP64 check fields are
+ * not evaluated in batches). */
+ELBM_API elbm_status elbm_batch_entropy_stats(elbm_batch *b, int id,
+                                              elbm_entropy_stats_t *out);
+/* Launch configuration in use (after the first step: the tuned one). */
+ELBM_API elbm_status elbm_batch_tuning(const elbm_batch *b, int *threads,
+                                       int *blocks_per_sm, int *burst);
+ELBM_API size_t elbm_batch_device_bytes(const elbm_batch *b);
+
 /* Reference density rho0 of the shifted storage (meaningful after init). */
 ELBM_API double elbm_rho0(const elbm_handle *h);
 

@@ -80,6 +80,12 @@ class EntropyStats(ctypes.Structure):
         return out
 
 
+class MemberSpec(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_int), ("nx", ctypes.c_int),
+                ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("nu", ctypes.c_double)]
+
+
 _lib = None
 _P = ctypes.c_void_p
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -119,6 +125,31 @@ SIGNATURES = {
                                         ctypes.c_double, ctypes.c_double, _P,
                                         _P, _P, _P,
                                         ctypes.POINTER(EntropyStats)]),
+    "elbm_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int]),
+    "elbm_batch_destroy": (None, [_P]),
+    "elbm_batch_last_error": (ctypes.c_char_p, [_P]),
+    "elbm_batch_set_stream": (ctypes.c_int, [_P, _P]),
+    "elbm_batch_set_allocator": (ctypes.c_int, [_P, ALLOC_FN, FREE_FN, _P]),
+    "elbm_batch_set_options": (ctypes.c_int, [_P] + [ctypes.c_int] * 4),
+    "elbm_batch_add": (ctypes.c_int, [_P, ctypes.POINTER(MemberSpec), _DP,
+                                      _DP, ctypes.POINTER(ctypes.c_int)]),
+    "elbm_batch_remove": (ctypes.c_int, [_P, ctypes.c_int]),
+    "elbm_batch_set_steps": (ctypes.c_int, [_P, ctypes.c_int,
+                                            ctypes.c_longlong]),
+    "elbm_batch_member_info": (ctypes.c_int, [_P, ctypes.c_int, _LLP, _LLP]),
+    "elbm_batch_record_alpha": (ctypes.c_int, [_P, ctypes.c_int,
+                                               ctypes.c_int]),
+    "elbm_batch_step": (ctypes.c_int, [_P, ctypes.c_longlong]),
+    "elbm_batch_sync": (ctypes.c_int, [_P]),
+    "elbm_batch_moments": (ctypes.c_int, [_P, ctypes.c_int, _DP, _DP]),
+    "elbm_batch_get_populations": (ctypes.c_int, [_P, ctypes.c_int, _DP]),
+    "elbm_batch_alpha_map": (ctypes.c_int, [_P, ctypes.c_int, _FP]),
+    "elbm_batch_entropy_stats": (ctypes.c_int, [_P, ctypes.c_int,
+                                                ctypes.POINTER(EntropyStats)]),
+    "elbm_batch_tuning": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int)]),
+    "elbm_batch_device_bytes": (ctypes.c_size_t, [_P]),
     "elbm_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
     "elbm_profile": (ctypes.c_int, [_P, _DP, _LLP]),
 }
@@ -332,3 +363,145 @@ class Lattice:
     def beta(self):
         cs2 = 1.0 / 3.0
         return cs2 / (2.0 * self.nu + cs2)
+
+
+class Batch:
+    """Many independent periodic lattices (FP32-shifted storage, FORMULA
+    alpha) advanced together by the batched persistent kernel.
+
+    Members are added with ``add(lattice, nx, ny, nz, nu, rho, u)`` and get
+    an integer id; ``step(n)`` advances every member that still has steps
+    (``set_steps(id, k)`` limits a member to k more steps).
+    """
+
+    def __init__(self, max_members=256, burst=16, use_graphs=True,
+                 autotune=True, diag_every=0, allocator=None, stream=None):
+        L = lib()
+        h = _P()
+        st = L.elbm_batch_create(ctypes.byref(h), int(max_members))
+        if st:
+            raise ElbmError(st, L.elbm_last_error(None).decode())
+        self._h = h
+        torch = _torch_cuda()
+        if allocator is None:
+            allocator = "torch" if torch is not None else "cuda"
+        self._cb = None
+        if allocator == "torch":
+            dev = torch.cuda.current_device()
+
+            def _alloc(size, ctx):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(size), dev)
+                except Exception:
+                    return None
+
+            def _free(ptr, ctx):
+                torch.cuda.caching_allocator_delete(int(ptr))
+
+            self._cb = (ALLOC_FN(_alloc), FREE_FN(_free))
+            self._check(L.elbm_batch_set_allocator(h, self._cb[0],
+                                                   self._cb[1], None))
+        if stream is None and torch is not None:
+            stream = torch.cuda.current_stream().cuda_stream
+        if stream is not None:
+            self._check(L.elbm_batch_set_stream(h, _P(int(stream))))
+        self.set_options(diag_every, burst, use_graphs, autotune)
+        self.members = {}
+
+    def _check(self, st):
+        if st:
+            raise ElbmError(st, lib().elbm_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().elbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_options(self, diag_every=0, burst=16, use_graphs=True,
+                    autotune=True):
+        self._check(lib().elbm_batch_set_options(
+            self._h, int(diag_every), int(burst), int(bool(use_graphs)),
+            int(bool(autotune))))
+
+    def add(self, lattice, nx, ny, nz, nu, rho, u):
+        lat = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
+        spec = MemberSpec(lat, int(nx), int(ny), int(nz), float(nu))
+        shape = (int(nz), int(ny), int(nx))
+        r = np.ascontiguousarray(np.broadcast_to(rho, shape), dtype=np.float64)
+        v = np.ascontiguousarray(u, dtype=np.float64)
+        mid = ctypes.c_int()
+        self._check(lib().elbm_batch_add(self._h, ctypes.byref(spec),
+                                         _dptr(r), _dptr(v),
+                                         ctypes.byref(mid)))
+        self.members[mid.value] = (lat, shape)
+        return mid.value
+
+    def remove(self, mid):
+        self._check(lib().elbm_batch_remove(self._h, int(mid)))
+        self.members.pop(mid, None)
+
+    def set_steps(self, mid, remaining):
+        self._check(lib().elbm_batch_set_steps(self._h, int(mid),
+                                               int(remaining)))
+
+    def info(self, mid):
+        done = ctypes.c_longlong()
+        rem = ctypes.c_longlong()
+        self._check(lib().elbm_batch_member_info(
+            self._h, int(mid), ctypes.byref(done), ctypes.byref(rem)))
+        return done.value, rem.value
+
+    def record_alpha(self, mid, enable=True):
+        self._check(lib().elbm_batch_record_alpha(self._h, int(mid),
+                                                  int(bool(enable))))
+
+    def step(self, nsteps):
+        self._check(lib().elbm_batch_step(self._h, int(nsteps)))
+
+    def sync(self):
+        self._check(lib().elbm_batch_sync(self._h))
+
+    def moments(self, mid):
+        lat, shape = self.members[mid]
+        rho = np.empty(shape)
+        u = np.empty((DIM[lat],) + shape)
+        self._check(lib().elbm_batch_moments(self._h, int(mid), _dptr(rho),
+                                             _dptr(u)))
+        return rho, u
+
+    def populations(self, mid):
+        lat, shape = self.members[mid]
+        f = np.empty((Q[lat],) + shape)
+        self._check(lib().elbm_batch_get_populations(self._h, int(mid),
+                                                     _dptr(f)))
+        return f
+
+    def alpha_map(self, mid):
+        lat, shape = self.members[mid]
+        a = np.empty(shape, dtype=np.float32)
+        self._check(lib().elbm_batch_alpha_map(self._h, int(mid),
+                                               a.ctypes.data_as(_FP)))
+        return a
+
+    def entropy_stats(self, mid):
+        s = EntropyStats()
+        self._check(lib().elbm_batch_entropy_stats(self._h, int(mid),
+                                                   ctypes.byref(s)))
+        return s.as_dict()
+
+    def tuning(self):
+        t, b, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(lib().elbm_batch_tuning(self._h, ctypes.byref(t),
+                                            ctypes.byref(b), ctypes.byref(k)))
+        return {"threads": t.value, "blocks_per_sm": b.value,
+                "burst": k.value}
+
+    @property
+    def device_bytes(self):
+        return lib().elbm_batch_device_bytes(self._h)

@@ -1,0 +1,299 @@
+// Batched stream-collide over many independent periodic lattices in one
+// persistent launch (FP32-shifted storage, FORMULA).
+//
+// Members may differ in lattice type (D2Q9 / D3Q27), size and viscosity.
+// Each member's lattice is cut into tiles of TB consecutive nodes; the tiles
+// of all stepping members form one flat list whose prefix offsets live in
+// device memory, so a launch (or a captured CUDA graph of launches) reads
+// the current membership at run time.  Blocks walk the list with a grid
+// stride and the same cp.async double-buffered gather / shared-memory
+// compute as the single-lattice kernel; a tile's block switches on its
+// member's lattice type (uniform per block).
+//
+// A burst is a sequence of steps s = 0, 1, ...; member m takes part in
+// steps s < steps_left(m) and reads buf[(parity0 + s) & 1], writes the other
+// buffer; its tiles are skipped in later steps of the burst.  Members with
+// no steps left are left out of the tile list.
+#pragma once
+#include <stdint.h>
+
+#include "sc32.cuh"
+
+namespace elbm {
+
+constexpr int kBatchMaxMembers = 256;
+
+struct MemberDesc {
+  float* buf[2];        // FP32-shifted pull-layout populations (select with
+                        // pick(): a runtime index would force local memory)
+  float* alpha_map;     // nullable
+  unsigned n;           // nodes
+  int nx, ny, nz;
+  FastDiv div_nx, div_ny;
+  float beta;
+  float rho0f;
+  double rho0;
+  double beta64;        // beta of Eq. (2) in FP64 (far-node fixup)
+  int lattice;          // 0: D2Q9, 1: D3Q27
+  int parity0;          // buffer holding f^n at burst step 0
+  int steps_left;       // steps of this burst the member takes
+  int diag;             // accumulate statistics on its last burst step
+};
+
+// Per-member statistics of one step (atomically accumulated).
+struct MemberStats {
+  double drho, j0, j1, j2, ke, asum;
+  unsigned long long nodes, acc2, formula, band, degen, far;
+  unsigned amin_bits, amax_bits;   // positive floats: integer order
+};
+
+struct BatchParams {
+  const MemberDesc* members;
+  const unsigned* tile_begin;   // [count + 1] tile prefix of the members
+  const int* count;             // members in the tile list
+  MemberStats* stats;           // [kBatchMaxMembers]
+  unsigned long long* far_queue;   // (member << 32) | node
+  unsigned far_cap;
+  unsigned* far_count;          // [2]
+  unsigned* err_flags;
+  int step;                     // step index within the burst
+};
+
+__device__ __forceinline__ float* pick(const MemberDesc& m, int parity) {
+  return (parity & 1) ? m.buf[1] : m.buf[0];
+}
+
+__device__ __forceinline__ int find_member(const unsigned* begin, int count,
+                                           unsigned tile) {
+  int lo = 0, hi = count;   // begin[lo] <= tile < begin[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (begin[mid] <= tile)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+template <class L, int TB>
+__device__ __forceinline__ void batch_issue(const MemberDesc& m, int step,
+                                            float* sm, unsigned local) {
+  const unsigned node = local * TB + threadIdx.x;
+  if (node >= m.n) return;
+  const unsigned q1 = m.div_nx.div(node);
+  const int x = (int)(node - q1 * (unsigned)m.nx);
+  const unsigned q2 = m.div_ny.div(q1);
+  const int y = (int)(q1 - q2 * (unsigned)m.ny), z = (int)q2;
+  const int xm = x == 0 ? m.nx - 1 : x - 1, xp = x == m.nx - 1 ? 0 : x + 1;
+  const int ym = y == 0 ? m.ny - 1 : y - 1, yp = y == m.ny - 1 ? 0 : y + 1;
+  const int zm = z == 0 ? m.nz - 1 : z - 1, zp = z == m.nz - 1 ? 0 : z + 1;
+  const float* in = pick(m, m.parity0 + step);
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+    const int xs = cx == 1 ? xm : (cx == -1 ? xp : x);
+    const int ys = cy == 1 ? ym : (cy == -1 ? yp : y);
+    const int zs = cz == 1 ? zm : (cz == -1 ? zp : z);
+    const unsigned off =
+        ((unsigned)zs * (unsigned)m.ny + (unsigned)ys) * (unsigned)m.nx +
+        (unsigned)xs;
+    cp_async4(sm + i * TB + threadIdx.x, in + off);
+    in += m.n;   // next population array
+  }
+}
+
+// Block reduction of one tile's statistics into the member's record.
+template <int TB>
+__device__ __forceinline__ void batch_tile_stats(const Acc32& a,
+                                                 MemberStats* st) {
+  __shared__ double red[TB / 32][6];
+  __shared__ unsigned long long redc[TB / 32][5];
+  __shared__ float redm[TB / 32][2];
+  double v[6] = {a.drho.value(), a.j0.value(), a.j1.value(), a.j2.value(),
+                 a.ke.value(), a.asum.value()};
+  unsigned long long c[5] = {a.nodes, a.acc2, a.formula, a.band, a.degen};
+  float mn = a.amin, mx = a.amax;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) c[k] += __shfl_xor_sync(0xffffffffu, c[k], o);
+    mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) red[w][k] = v[k];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) redc[w][k] = c[k];
+    redm[w][0] = mn;
+    redm[w][1] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int ww = 1; ww < TB / 32; ++ww) {
+      for (int k = 0; k < 6; ++k) red[0][k] += red[ww][k];
+      for (int k = 0; k < 5; ++k) redc[0][k] += redc[ww][k];
+      redm[0][0] = fminf(redm[0][0], redm[ww][0]);
+      redm[0][1] = fmaxf(redm[0][1], redm[ww][1]);
+    }
+    if (redc[0][0] > 0) {
+      atomicAdd(&st->drho, red[0][0]);
+      atomicAdd(&st->j0, red[0][1]);
+      atomicAdd(&st->j1, red[0][2]);
+      atomicAdd(&st->j2, red[0][3]);
+      atomicAdd(&st->ke, red[0][4]);
+      atomicAdd(&st->asum, red[0][5]);
+      atomicAdd(&st->nodes, redc[0][0]);
+      atomicAdd(&st->acc2, redc[0][1]);
+      atomicAdd(&st->formula, redc[0][2]);
+      atomicAdd(&st->band, redc[0][3]);
+      atomicAdd(&st->degen, redc[0][4]);
+      atomicMin(&st->amin_bits, __float_as_uint(redm[0][0]));
+      atomicMax(&st->amax_bits, __float_as_uint(redm[0][1]));
+    }
+  }
+  __syncthreads();
+}
+
+template <int TB, int DIAG>
+__global__ void __launch_bounds__(TB, 2048 / TB / 4)
+    k_batch(const BatchParams bp) {
+  extern __shared__ float smem[];   // [2][27][TB]
+  __shared__ unsigned s_begin[kBatchMaxMembers + 1];
+  const int count = *bp.count;
+  for (int k = threadIdx.x; k <= count; k += TB) s_begin[k] = bp.tile_begin[k];
+  __syncthreads();
+  const unsigned total = s_begin[count];
+  constexpr int kStage = 27 * TB;
+
+  unsigned tile = blockIdx.x;
+  int stage = 0;
+  auto issue = [&](unsigned t, float* sm) {
+    const int mi = find_member(s_begin, count, t);
+    const MemberDesc m = bp.members[mi];   // by value: no reloads after stores
+    if (bp.step >= m.steps_left) return;   // member finished in this burst
+    const unsigned local = t - s_begin[mi];
+    if (m.lattice == 1)
+      batch_issue<D3Q27, TB>(m, bp.step, sm, local);
+    else
+      batch_issue<D2Q9, TB>(m, bp.step, sm, local);
+  };
+  if (tile < total) issue(tile, smem);
+  cp_async_commit();
+  for (; tile < total; tile += gridDim.x) {
+    const unsigned next = tile + gridDim.x;
+    if (next < total) issue(next, smem + (stage ^ 1) * kStage);
+    cp_async_commit();
+    cp_async_wait<1>();
+    const float* sm = smem + stage * kStage + threadIdx.x;
+    stage ^= 1;
+
+    const int mi = find_member(s_begin, count, tile);
+    const MemberDesc m = bp.members[mi];   // by value: no reloads after stores
+    if (bp.step >= m.steps_left) continue;   // uniform per block
+    const unsigned node = (tile - s_begin[mi]) * TB + threadIdx.x;
+    const bool stats_step = DIAG && m.diag && bp.step == m.steps_left - 1;
+    Acc32 acc;
+    if (DIAG) acc.init();
+    if (node < m.n) {
+      float* out = pick(m, m.parity0 + bp.step + 1);
+      float* amap = m.alpha_map ? m.alpha_map + node : nullptr;
+      bool ok;
+      auto store = [&](int i, float v) { out[(size_t)i * m.n + node] = v; };
+      if (m.lattice == 1)
+        ok = sc32_node<D3Q27, true, DIAG, 0, TB>(sm, m.rho0f, m.rho0, m.beta,
+                                                 0.0f, nullptr, amap, acc,
+                                                 store);
+      else
+        ok = sc32_node<D2Q9, true, DIAG, 0, TB>(sm, m.rho0f, m.rho0, m.beta,
+                                                0.0f, nullptr, amap, acc,
+                                                store);
+      if (!ok) {
+        const unsigned slot = atomicAdd(&bp.far_count[bp.step & 1], 1u);
+        if (slot < bp.far_cap)
+          bp.far_queue[slot] = ((unsigned long long)mi << 32) | node;
+        else
+          atomicOr(bp.err_flags, NF_BAD_NONFINITE);   // cannot happen
+      }
+    }
+    if (DIAG) {
+      // uniform per block: the whole tile belongs to member mi
+      if (stats_step) batch_tile_stats<TB>(acc, bp.stats + mi);
+    }
+  }
+  cp_async_wait<0>();
+}
+
+// FP64 FORMULA for the nodes the batch kernel deferred; clears the other
+// parity's counter for the next step.
+template <int DIAG>
+__global__ void __launch_bounds__(256) k_batch_fixup(const BatchParams bp) {
+  const unsigned count = min(bp.far_count[bp.step & 1], bp.far_cap);
+  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < count;
+       k += gridDim.x * blockDim.x) {
+    const unsigned long long e = bp.far_queue[k];
+    const int mi = (int)(e >> 32);
+    const unsigned node = (unsigned)(e & 0xffffffffu);
+    const MemberDesc& m = bp.members[mi];
+    const float* in = pick(m, m.parity0 + bp.step);
+    float* out = pick(m, m.parity0 + bp.step + 1);
+    StepParams g;   // geometry for src_index
+    g.nx = m.nx;
+    g.ny = m.ny;
+    g.nz = m.nz;
+    const int x = (int)(node % (unsigned)m.nx);
+    const int y = (int)((node / (unsigned)m.nx) % (unsigned)m.ny);
+    const int z = (int)(node / ((unsigned)m.nx * (unsigned)m.ny));
+    Acc acc;
+    acc.init();
+    StepParams pp;
+    pp.beta = m.beta64;
+    pp.rho0 = m.rho0;
+    pp.err_flags = bp.err_flags;
+    pp.secant_iters = 1;
+    pp.alpha_map = m.alpha_map;
+    auto run = [&](auto lat) {
+      using L = decltype(lat);
+      Node64<L> nd;
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i)
+        nd.f[i] = L::w(i) * m.rho0 +
+                  (double)in[(size_t)i * m.n + src_index<L>(g, i, x, y, z)];
+      auto store = [&](int i, double v) {
+        if (i < 0) {
+          m.alpha_map[node] = (float)v;
+        } else {
+          out[(size_t)i * m.n + node] = (float)(v - L::w(i) * m.rho0);
+        }
+      };
+      collide64<L, MODE_FORMULA, 0>(nd, pp, true, acc, DIAG != 0, store);
+    };
+    if (m.lattice == 1)
+      run(D3Q27{});
+    else
+      run(D2Q9{});
+    if (DIAG && m.diag && bp.step == m.steps_left - 1 && acc.nodes > 0) {
+      MemberStats* st = bp.stats + mi;
+      atomicAdd(&st->drho, acc.drho);
+      atomicAdd(&st->j0, acc.j0);
+      atomicAdd(&st->j1, acc.j1);
+      atomicAdd(&st->j2, acc.j2);
+      atomicAdd(&st->ke, acc.ke);
+      atomicAdd(&st->asum, acc.asum);
+      atomicAdd(&st->nodes, 1ull);
+      atomicAdd(&st->far, 1ull);
+      atomicAdd(&st->acc2, (unsigned long long)acc.acc2);
+      atomicAdd(&st->formula, (unsigned long long)acc.formula);
+      const float a = (float)acc.asum;
+      atomicMin(&st->amin_bits, __float_as_uint(a));
+      atomicMax(&st->amax_bits, __float_as_uint(a));
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) bp.far_count[(bp.step & 1) ^ 1] = 0u;
+}
+
+}  // namespace elbm

@@ -10,6 +10,7 @@ namespace elbm {
 
 // Launch counter shared by all launch sites.
 void count_launch();
+void count_launches(long long n);
 
 // Message returned by elbm_last_error(NULL) (thread-local).
 void set_global_error(const std::string& msg);

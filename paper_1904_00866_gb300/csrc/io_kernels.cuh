@@ -1,0 +1,176 @@
+// Initialisation and readout kernels of the pull-layout storage (FP64,
+// FP32 or FP32-shifted populations), shared by the single-lattice runtime
+// and the batched runtime.
+#pragma once
+#include <math.h>
+
+#include "lattice.cuh"
+#include "node_fp64.cuh"
+
+namespace elbm {
+
+// ------------------------------------------------------------------------
+// Initialisation / readout kernels (grid-stride over nodes).
+// ------------------------------------------------------------------------
+
+// Entropic equilibrium in FP64: per-axis factors 1 + d(c), d(0) = -s,
+// d(+-1) = +-3u + 2s, s = 3u^2 / (1 + sqrt(1 + 3u^2)).
+template <class L>
+__device__ __forceinline__ void equilibrium_dev(double rho, const double* u,
+                                                double rho0, double* dev_out,
+                                                double* f_out) {
+  double dp[3], dm[3], d0[3];
+#pragma unroll
+  for (int a = 0; a < L::D; ++a) {
+    const double s = 3.0 * u[a] * u[a] / (1.0 + sqrt(1.0 + 3.0 * u[a] * u[a]));
+    dp[a] = 3.0 * u[a] + 2.0 * s;
+    dm[a] = -3.0 * u[a] + 2.0 * s;
+    d0[a] = -s;
+  }
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    double pm1 = 0.0;   // prod (1 + d) - 1
+#pragma unroll
+    for (int a = 0; a < L::D; ++a) {
+      const int c = L::c(i, a);
+      const double d = c == 1 ? dp[a] : (c == -1 ? dm[a] : d0[a]);
+      pm1 = fma(pm1, d, pm1 + d);
+    }
+    // f^eq_i - W_i rho0 = W_i ((rho - rho0) + rho (P_i - 1))
+    dev_out[i] = L::w(i) * ((rho - rho0) + rho * pm1);
+    f_out[i] = L::w(i) * rho * (1.0 + pm1);
+  }
+}
+
+// Storage value of a population f whose deviation from W_i rho0 is dev.
+template <class T>
+__device__ __forceinline__ T to_storage(double f, double dev, int shifted) {
+  if (sizeof(T) == 8) return (T)f;
+  return shifted ? (T)dev : (T)f;
+}
+
+struct Geo {
+  int nx, ny, nz;
+  long long n;
+  double rho0;
+  int shifted;   // FP32_SHIFTED storage
+};
+
+template <class L>
+__device__ __forceinline__ long long shifted_node(const Geo& g, long long node,
+                                                  int i, int sign) {
+  // node + sign * c_i (periodic)
+  int x = (int)(node % g.nx);
+  int y = (int)((node / g.nx) % g.ny);
+  int z = (int)(node / ((long long)g.nx * g.ny));
+  x += sign * L::c(i, 0);
+  y += sign * L::c(i, 1);
+  z += sign * L::c(i, 2);
+  x = x < 0 ? x + g.nx : (x >= g.nx ? x - g.nx : x);
+  y = y < 0 ? y + g.ny : (y >= g.ny ? y - g.ny : y);
+  z = z < 0 ? z + g.nz : (z >= g.nz ? z - g.nz : z);
+  return ((long long)z * g.ny + y) * g.nx + x;
+}
+
+// f^0 = f^eq(rho, u); stored at x - c_i so that the pull gather of step 0
+// returns it at x.
+template <class L, class T>
+__global__ void k_init_feq(Geo g, const double* __restrict__ rho,
+                           const double* __restrict__ u, void* fv,
+                           unsigned* err) {
+  T* __restrict__ f = static_cast<T*>(fv);
+  for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+       node < g.n; node += (long long)gridDim.x * blockDim.x) {
+    double uu[3] = {0.0, 0.0, 0.0};
+    const double r = rho[node];
+    bool bad = !(r > 0.0) || !isfinite(r);
+#pragma unroll
+    for (int a = 0; a < L::D; ++a) {
+      uu[a] = u[a * g.n + node];
+      bad |= !(fabs(uu[a]) < 1.0);
+    }
+    if (bad) atomicOr(err, NF_BAD_NONFINITE);
+    double dev[L::Q], fe[L::Q];
+    equilibrium_dev<L>(bad ? 1.0 : r, uu, g.rho0, dev, fe);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i)
+      f[i * g.n + shifted_node<L>(g, node, i, -1)] =
+          to_storage<T>(fe[i], dev[i], g.shifted);
+  }
+}
+
+// Pre-collision populations f^n (FP64, [Q][N]) -> pull storage.
+template <class L, class T>
+__global__ void k_set_pop(Geo g, const double* __restrict__ fin, void* fv) {
+  T* __restrict__ f = static_cast<T*>(fv);
+  for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+       node < g.n; node += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      const double v = fin[i * g.n + node];
+      const double s = L::w(i) * g.rho0;
+      f[i * g.n + shifted_node<L>(g, node, i, -1)] =
+          to_storage<T>(v, v - s, g.shifted);
+    }
+  }
+}
+
+template <class L, class T>
+__device__ __forceinline__ double load_pre(const Geo& g, const T* f,
+                                           long long node, int i) {
+  const double v = (double)f[i * g.n + shifted_node<L>(g, node, i, -1)];
+  if (sizeof(T) == 4 && g.shifted) return L::w(i) * g.rho0 + v;
+  return v;
+}
+
+// Storage -> pre-collision populations / moments (gather).
+template <class L, class T>
+__global__ void k_get_pop(Geo g, const void* fv, double* __restrict__ out) {
+  const T* __restrict__ f = static_cast<const T*>(fv);
+  for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+       node < g.n; node += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) out[i * g.n + node] = load_pre<L, T>(g, f, node, i);
+  }
+}
+
+template <class L, class T>
+__global__ void k_get_nodes(Geo g, const void* fv,
+                            const long long* __restrict__ nodes, int count,
+                            double* __restrict__ out) {
+  const T* __restrict__ f = static_cast<const T*>(fv);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count;
+       k += gridDim.x * blockDim.x) {
+    const long long node = nodes[k];
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i)
+      out[(long long)k * L::Q + i] = load_pre<L, T>(g, f, node, i);
+  }
+}
+
+template <class L, class T>
+__global__ void k_moments(Geo g, const void* fv, double* __restrict__ rho_out,
+                          double* __restrict__ u_out) {
+  const T* __restrict__ f = static_cast<const T*>(fv);
+  for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+       node < g.n; node += (long long)gridDim.x * blockDim.x) {
+    double rho = 0.0, j[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      const double v = load_pre<L, T>(g, f, node, i);
+      rho += v;
+#pragma unroll
+      for (int a = 0; a < L::D; ++a) {
+        if (L::c(i, a) == 1) j[a] += v;
+        if (L::c(i, a) == -1) j[a] -= v;
+      }
+    }
+    if (rho_out) rho_out[node] = rho;
+    if (u_out) {
+#pragma unroll
+      for (int a = 0; a < L::D; ++a) u_out[a * g.n + node] = j[a] / rho;
+    }
+  }
+}
+
+}  // namespace elbm

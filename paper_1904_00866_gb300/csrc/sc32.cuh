@@ -97,6 +97,74 @@ __device__ __forceinline__ void issue_tile(const StepParams& p, float* sm,
   }
 }
 
+// Collision of one node whose Q gathered values sit in shared memory at
+// sm[i * TB] (this thread's column).  Writes the Q post-collision values
+// through out(i, value) and the alpha through amap (nullable).  Returns
+// false when the node must go to the FP64 fixup (nothing written).
+template <class L, bool SHIFTED, int DIAG, int CHECK, int TB, class Out>
+__device__ __forceinline__ bool sc32_node(const float* sm, float rho0f,
+                                          double rho0, float beta,
+                                          float corr_rho,
+                                          const float* __restrict__ corr,
+                                          float* amap, Acc32& acc, Out out) {
+  constexpr int Q = L::Q;
+  float d[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const float v = sm[i * TB];
+    d[i] = SHIFTED ? v : v - L::wf(i) * rho0f;
+  }
+  float a_extra = 0.0f;
+  if (!SHIFTED) {
+    // delta_i = v_i - s_i is exact unless v_i leaves [s_i/2, 2 s_i]
+    float A = 0.0f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) A += fabsf(d[i]);
+    a_extra = 2.0f * 5.9604645e-8f * A / rho0f;
+  }
+  N32<L> r;
+  node32_formula<L, SHIFTED>(d, rho0f, corr_rho, corr, a_extra, r);
+  if (r.flags & NF_FAR) return false;
+  // relax with the conservation-projected n:  f~ = f + alpha beta n
+  const float ab = r.alpha * beta;
+  projection<L>(r.n, [&](int i, float wt) {
+    const float nv = fmaf(ab, r.n[i] - wt, d[i]);
+    out(i, SHIFTED ? nv : nv + L::wf(i) * rho0f);
+  });
+  if (amap) *amap = r.alpha;
+  if (DIAG) {
+    acc.nodes += 1;
+    acc.drho.add(r.drho);
+    acc.j0.add(r.j[0]);
+    acc.j1.add(r.j[1]);
+    acc.j2.add(r.j[2]);
+    acc.ke.add(0.5f * (r.j[0] * r.j[0] + r.j[1] * r.j[1] + r.j[2] * r.j[2]) /
+               r.rho);
+    acc.asum.add(r.alpha);
+    acc.amin = fminf(acc.amin, r.alpha);
+    acc.amax = fmaxf(acc.amax, r.alpha);
+    acc.acc2 += (r.flags & NF_ACCEPT_TWO) != 0;
+    acc.formula += (r.flags & NF_FORMULA) != 0;
+    acc.band += (r.flags & NF_BAND) != 0;
+    acc.degen += (r.flags & NF_DEGENERATE) != 0;
+    if (CHECK) {
+      Node64<L> nd;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const double v = (double)sm[i * TB];
+        nd.f[i] = SHIFTED ? L::w(i) * rho0 + v : v;
+      }
+      node64_prepare(nd);
+      Check64 ck = node64_check(nd, (double)r.alpha);
+      acc.h += ck.h;
+      acc.viol += ck.violation;
+      acc.mismatch += ((r.flags & NF_ACCEPT_STAR) != 0) != ck.accept_ref;
+      acc.adev = fmax(acc.adev, fabs((double)r.alpha - ck.alpha_ref));
+    }
+  }
+  return true;
+}
+
 template <class L, bool SHIFTED, int DIAG, int CHECK>
 __global__ void __launch_bounds__(kSc32Threads, 2)
     k_sc32(const StepParams p) {
@@ -123,24 +191,11 @@ __global__ void __launch_bounds__(kSc32Threads, 2)
     const float* sm = smem + stage * Q * kSc32Threads + threadIdx.x;
     stage ^= 1;
     if (node >= (unsigned)p.n) continue;
-
-    float d[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const float v = sm[i * kSc32Threads];
-      d[i] = SHIFTED ? v : v - L::wf(i) * rho0f;
-    }
-    float a_extra = 0.0f;
-    if (!SHIFTED) {
-      // delta_i = v_i - s_i is exact unless v_i leaves [s_i/2, 2 s_i]
-      float A = 0.0f;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) A += fabsf(d[i]);
-      a_extra = 2.0f * 5.9604645e-8f * A / rho0f;
-    }
-    N32<L> r;
-    node32_formula<L, SHIFTED>(d, rho0f, p.corr_rho, p.corr, a_extra, r);
-    if (r.flags & NF_FAR) {
+    const bool done = sc32_node<L, SHIFTED, DIAG, CHECK, kSc32Threads>(
+        sm, rho0f, p.rho0, beta, p.corr_rho, p.corr,
+        p.alpha_map ? p.alpha_map + node : nullptr, acc,
+        [&](int i, float v) { p.out_pop[i][node] = v; });
+    if (!done) {
       // far from (or invalid, or within FP32 noise of) equilibrium: the FP64
       // fixup collides this node from f_in
       const unsigned slot = atomicAdd(&p.far_count[p.parity], 1u);
@@ -148,44 +203,6 @@ __global__ void __launch_bounds__(kSc32Threads, 2)
         p.far_queue[slot] = node;
       else
         atomicOr(p.err_flags, NF_BAD_NONFINITE);   // cannot happen: cap = n
-      continue;
-    }
-    // relax with the conservation-projected n:  f~ = f + alpha beta n
-    const float ab = r.alpha * beta;
-    projection<L>(r.n, [&](int i, float wt) {
-      const float nv = fmaf(ab, r.n[i] - wt, d[i]);
-      p.out_pop[i][node] = SHIFTED ? nv : nv + L::wf(i) * rho0f;
-    });
-    if (p.alpha_map) p.alpha_map[node] = r.alpha;
-    if (DIAG) {
-      acc.nodes += 1;
-      acc.drho.add(r.drho);
-      acc.j0.add(r.j[0]);
-      acc.j1.add(r.j[1]);
-      acc.j2.add(r.j[2]);
-      acc.ke.add(0.5f * (r.j[0] * r.j[0] + r.j[1] * r.j[1] +
-                         r.j[2] * r.j[2]) / r.rho);
-      acc.asum.add(r.alpha);
-      acc.amin = fminf(acc.amin, r.alpha);
-      acc.amax = fmaxf(acc.amax, r.alpha);
-      acc.acc2 += (r.flags & NF_ACCEPT_TWO) != 0;
-      acc.formula += (r.flags & NF_FORMULA) != 0;
-      acc.band += (r.flags & NF_BAND) != 0;
-      acc.degen += (r.flags & NF_DEGENERATE) != 0;
-      if (CHECK) {
-        Node64<L> nd;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-          const double v = (double)sm[i * kSc32Threads];
-          nd.f[i] = SHIFTED ? L::w(i) * p.rho0 + v : v;
-        }
-        node64_prepare(nd);
-        Check64 ck = node64_check(nd, (double)r.alpha);
-        acc.h += ck.h;
-        acc.viol += ck.violation;
-        acc.mismatch += ((r.flags & NF_ACCEPT_STAR) != 0) != ck.accept_ref;
-        acc.adev = fmax(acc.adev, fabs((double)r.alpha - ck.alpha_ref));
-      }
     }
   }
   cp_async_wait<0>();
