@@ -205,6 +205,11 @@ ELBM_API elbm_status elbm_alpha_map(elbm_handle *h, float *alpha_out);
  * Synchronises. */
 ELBM_API elbm_status elbm_entropy_stats(elbm_handle *h, elbm_entropy_stats_t *out);
 
+/* Enstrophy 1/2 <|omega|^2> of f^n: omega = curl u by second-order central
+ * differences on the periodic lattice (2D: omega_z), averaged over nodes.
+ * Synchronises. */
+ELBM_API elbm_status elbm_enstrophy(elbm_handle *h, double *out);
+
 /* Steps taken since the last initialisation. */
 ELBM_API long long elbm_step_count(const elbm_handle *h);
 

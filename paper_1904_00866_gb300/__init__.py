@@ -116,6 +116,7 @@ SIGNATURES = {
                                                   _DP]),
     "elbm_alpha_map": (ctypes.c_int, [_P, _FP]),
     "elbm_entropy_stats": (ctypes.c_int, [_P, ctypes.POINTER(EntropyStats)]),
+    "elbm_enstrophy": (ctypes.c_int, [_P, _DP]),
     "elbm_step_count": (ctypes.c_longlong, [_P]),
     "elbm_device_bytes": (ctypes.c_size_t, [_P]),
     "elbm_launch_count": (ctypes.c_longlong, []),
@@ -334,6 +335,11 @@ class Lattice:
         s = EntropyStats()
         self._check(lib().elbm_entropy_stats(self._h, ctypes.byref(s)))
         return s.as_dict()
+
+    def enstrophy(self):
+        out = ctypes.c_double()
+        self._check(lib().elbm_enstrophy(self._h, ctypes.byref(out)))
+        return out.value
 
     def set_profiling(self, enable=True):
         self._check(lib().elbm_set_profiling(self._h, int(bool(enable))))

@@ -173,4 +173,45 @@ __global__ void k_moments(Geo g, const void* fv, double* __restrict__ rho_out,
   }
 }
 
+// Block partial sums of |curl u|^2 (second-order central differences,
+// periodic) from a velocity field u[d][nz][ny][nx].  2D: omega_z only.
+template <int DIM>
+__global__ void k_vorticity2(Geo g, const double* __restrict__ u,
+                             double* __restrict__ partials) {
+  __shared__ double sm[256];
+  double acc = 0.0;
+  for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+       node < g.n; node += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(node % g.nx);
+    const int y = (int)((node / g.nx) % g.ny);
+    const int z = (int)(node / ((long long)g.nx * g.ny));
+    auto at = [&](int a, int xx, int yy, int zz) {
+      xx = xx < 0 ? xx + g.nx : (xx >= g.nx ? xx - g.nx : xx);
+      yy = yy < 0 ? yy + g.ny : (yy >= g.ny ? yy - g.ny : yy);
+      zz = zz < 0 ? zz + g.nz : (zz >= g.nz ? zz - g.nz : zz);
+      return u[a * g.n + ((long long)zz * g.ny + yy) * g.nx + xx];
+    };
+    const double dvdx = 0.5 * (at(1, x + 1, y, z) - at(1, x - 1, y, z));
+    const double dudy = 0.5 * (at(0, x, y + 1, z) - at(0, x, y - 1, z));
+    const double wz = dvdx - dudy;
+    double w2 = wz * wz;
+    if (DIM == 3) {
+      const double dwdy = 0.5 * (at(2, x, y + 1, z) - at(2, x, y - 1, z));
+      const double dvdz = 0.5 * (at(1, x, y, z + 1) - at(1, x, y, z - 1));
+      const double dudz = 0.5 * (at(0, x, y, z + 1) - at(0, x, y, z - 1));
+      const double dwdx = 0.5 * (at(2, x + 1, y, z) - at(2, x - 1, y, z));
+      const double wx = dwdy - dvdz, wy = dudz - dwdx;
+      w2 += wx * wx + wy * wy;
+    }
+    acc += w2;
+  }
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = sm[0];
+}
+
 }  // namespace elbm

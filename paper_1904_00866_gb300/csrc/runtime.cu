@@ -690,6 +690,36 @@ elbm_status elbm_entropy_stats(elbm_handle* h, elbm_entropy_stats_t* out) {
   return ELBM_OK;
 }
 
+elbm_status elbm_enstrophy(elbm_handle* h, double* out) {
+  if (!h || !out) return h ? fail(h, ELBM_EINVAL, "NULL output") : ELBM_EINVAL;
+  if (!h->allocated) return fail(h, ELBM_ESTATE, "fields not initialised");
+  elbm_status st = check_errors(h);
+  if (st) return st;
+  const size_t bytes = sizeof(double) * (1 + h->d) * h->n;
+  double* tmp = (double*)dev_alloc(h, bytes);
+  if (!tmp) return fail(h, ELBM_ENOMEM, "staging allocation failed");
+  Geo g = geo(h);
+  DISPATCH_LT(h, k_moments, g, h->f[h->cur], tmp, tmp + h->n);
+  const int grid = grid_for(h->n);
+  if (h->d == 3)
+    k_vorticity2<3><<<grid, 256, 0, h->stream>>>(g, tmp + h->n, h->partials);
+  else
+    k_vorticity2<2><<<grid, 256, 0, h->stream>>>(g, tmp + h->n, h->partials);
+  count_launch();
+  std::vector<double> rows(grid);
+  cudaError_t e = cudaMemcpyAsync(rows.data(), h->partials,
+                                  sizeof(double) * grid,
+                                  cudaMemcpyDeviceToHost, h->stream);
+  cudaError_t e2 = cudaStreamSynchronize(h->stream);
+  dev_free(h, tmp);
+  if (e != cudaSuccess) return cuda_fail(h, e, "copy enstrophy");
+  if (e2 != cudaSuccess) return cuda_fail(h, e2, "enstrophy");
+  double s = 0.0;
+  for (double r : rows) s += r;
+  *out = 0.5 * s / (double)h->n;
+  return ELBM_OK;
+}
+
 long long elbm_step_count(const elbm_handle* h) { return h ? h->step : -1; }
 
 size_t elbm_device_bytes(const elbm_handle* h) { return h ? h->bytes : 0; }

@@ -311,3 +311,21 @@ def test_device_resident_init_matches_host_init(elbm):
     a.step(5)
     b.step(5)
     assert np.array_equal(a.populations(), b.populations())
+
+
+@pytest.mark.parametrize("lat,shape,dtype,tol", [
+    ("D2Q9", (1, 40, 48), "fp64", 1e-12),
+    ("D3Q27", (12, 16, 20), "fp64", 1e-12),
+    ("D3Q27", (16, 16, 16), "fp32_shifted", 1e-5)])
+def test_enstrophy_matches_oracle(elbm, orc, lat, shape, dtype, tol):
+    nz, ny, nx = shape
+    if lat == "D2Q9":
+        rho, u = W.taylor_green_2d(nx, 0.05, ny=ny)
+    else:
+        rho, u = W.taylor_green_3d(nx, 0.05, ny=ny, nz=nz)
+    g, o = _pair(elbm, orc, lat, shape, 2e-3, dtype, rho, u)
+    g.step(15)
+    o.step(15)
+    eg, eo = g.enstrophy(), o.enstrophy()
+    assert eo > 0
+    assert abs(eg / eo - 1) < tol
