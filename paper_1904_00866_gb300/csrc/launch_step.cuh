@@ -3,6 +3,10 @@
 #pragma once
 #include "internal.h"
 #include "sc32.cuh"
+#include "sc32_tma.cuh"
+
+#include <stdlib.h>
+#include <string.h>
 
 namespace elbm {
 
@@ -92,11 +96,59 @@ static cudaError_t launch_sc32_s(int diag, int check, const StepParams& p,
   return launch_sc32_one<L, SHIFTED, 0, 0>(p, grid, s, grid_used);
 }
 
+// Bulk-copy (TMA) row staging for FP32-shifted lattices with nx % 256 == 0.
+template <class L, int DIAG, int CHECK>
+static cudaError_t launch_tma_one(const StepParams& p, int grid,
+                                  cudaStream_t s, int* grid_used) {
+  auto k = k_sc32_tma<L, DIAG, CHECK>;
+  const int smem = kTmaStages * L::Q * kTmaRow * (int)sizeof(float);
+  static bool configured = false;   // per instantiation
+  if (!configured) {
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    configured = true;
+  }
+  if (grid <= 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem);
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 8) per_sm = 8;
+    long long g = (long long)sms * per_sm;
+    const long long tiles = p.n / 256;
+    if (tiles < g) g = tiles;
+    grid = g < 1 ? 1 : (int)g;
+  }
+  if (grid_used) *grid_used = grid;
+  k<<<grid, 256, smem, s>>>(p);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// ELBM_SC32_VARIANT=tma selects the bulk-copy row-staging kernel for
+// lattices with nx % 256 == 0.  It reads exactly the algorithmic bytes but
+// runs slower on GB300 than the per-thread cp.async gather (about 16 vs 22
+// GLUPS for D3Q27 at 512^3: its single-row copies serialise on the mbarrier
+// wait), so the gather kernel is the default.
+static bool tma_allowed() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("ELBM_SC32_VARIANT");
+    v = (e && strcmp(e, "tma") == 0) ? 1 : 0;
+  }
+  return v == 1;
+}
+
 template <class L>
 static cudaError_t launch_sc32(int diag, int check, const StepParams& p,
                                int grid, cudaStream_t s, int* grid_used) {
   if (p.unshifted)
     return launch_sc32_s<L, false>(diag, check, p, grid, s, grid_used);
+  if (p.nx % 256 == 0 && tma_allowed()) {
+    if (check) return launch_tma_one<L, 1, 1>(p, grid, s, grid_used);
+    if (diag) return launch_tma_one<L, 1, 0>(p, grid, s, grid_used);
+    return launch_tma_one<L, 0, 0>(p, grid, s, grid_used);
+  }
   return launch_sc32_s<L, true>(diag, check, p, grid, s, grid_used);
 }
 

@@ -272,6 +272,8 @@ static elbm_status check_errors(elbm_handle* h) {
   e = cudaMemcpy(&flags, h->err_flags, sizeof(unsigned),
                  cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(h, e, "read error flags");
+  if (flags & NF_TIMEOUT)
+    return fail(h, ELBM_ECUDA, "a kernel's bounded copy wait timed out");
   if (flags & NF_BAD_NEG)
     return fail(h, ELBM_ENEGATIVE, "a node had a population <= 0");
   if (flags & NF_BAD_NONFINITE)

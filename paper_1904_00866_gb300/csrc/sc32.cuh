@@ -97,21 +97,21 @@ __device__ __forceinline__ void issue_tile(const StepParams& p, float* sm,
   }
 }
 
-// Collision of one node whose Q gathered values sit in shared memory at
-// sm[i * TB] (this thread's column).  Writes the Q post-collision values
-// through out(i, value) and the alpha through amap (nullable).  Returns
-// false when the node must go to the FP64 fixup (nothing written).
-template <class L, bool SHIFTED, int DIAG, int CHECK, int TB, class Out>
-__device__ __forceinline__ bool sc32_node(const float* sm, float rho0f,
-                                          double rho0, float beta,
-                                          float corr_rho,
-                                          const float* __restrict__ corr,
-                                          float* amap, Acc32& acc, Out out) {
+// Collision of one node whose Q gathered values are returned by in(i)
+// (shared memory).  Writes the Q post-collision values through
+// out(i, value) and the alpha through amap (nullable).  Returns false when
+// the node must go to the FP64 fixup (nothing written).
+template <class L, bool SHIFTED, int DIAG, int CHECK, class In, class Out>
+__device__ __forceinline__ bool sc32_node_in(In in, float rho0f, double rho0,
+                                             float beta, float corr_rho,
+                                             const float* __restrict__ corr,
+                                             float* amap, Acc32& acc,
+                                             Out out) {
   constexpr int Q = L::Q;
   float d[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const float v = sm[i * TB];
+    const float v = in(i);
     d[i] = SHIFTED ? v : v - L::wf(i) * rho0f;
   }
   float a_extra = 0.0f;
@@ -151,7 +151,7 @@ __device__ __forceinline__ bool sc32_node(const float* sm, float rho0f,
       Node64<L> nd;
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
-        const double v = (double)sm[i * TB];
+        const double v = (double)in(i);
         nd.f[i] = SHIFTED ? L::w(i) * rho0 + v : v;
       }
       node64_prepare(nd);
@@ -163,6 +163,18 @@ __device__ __forceinline__ bool sc32_node(const float* sm, float rho0f,
     }
   }
   return true;
+}
+
+// Same, with the values in a shared-memory column of stride TB.
+template <class L, bool SHIFTED, int DIAG, int CHECK, int TB, class Out>
+__device__ __forceinline__ bool sc32_node(const float* sm, float rho0f,
+                                          double rho0, float beta,
+                                          float corr_rho,
+                                          const float* __restrict__ corr,
+                                          float* amap, Acc32& acc, Out out) {
+  return sc32_node_in<L, SHIFTED, DIAG, CHECK>(
+      [&](int i) { return sm[i * TB]; }, rho0f, rho0, beta, corr_rho, corr,
+      amap, acc, out);
 }
 
 template <class L, bool SHIFTED, int DIAG, int CHECK>
