@@ -41,8 +41,8 @@ if ROOT not in sys.path:
 N_MAIN = 512
 U0 = 0.05
 RE = 1600.0
-BYTES_PER_LU = {("D3Q27", 4): 216, ("D3Q27", 8): 432, ("D2Q9", 4): 72,
-                ("D2Q9", 8): 144}
+BYTES_PER_LU = {("D3Q27", 4): 216, ("D3Q27", 8): 432, ("D3Q27", 2): 108,
+                ("D2Q9", 4): 72, ("D2Q9", 8): 144, ("D2Q9", 2): 36}
 FALLBACK_HBM_GBS = 6800.0
 
 # DRAM traffic of k_sc32<D3Q27, shifted> from one ncu capture (256^3 case,
@@ -81,6 +81,9 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=100)
+    ap.add_argument("--storage", default="fp32_shifted",
+                    choices=["fp32_shifted", "fp16_shifted"],
+                    help="population storage of the timed lattice")
     return ap.parse_args()
 
 
@@ -238,6 +241,22 @@ def secondary(elbm, stream):
         ms, kms, nk = time_steps(g, steps, mode, stream)
         out[key] = round(n2 * n2 * steps / (ms * 1e3), 1)
         g.close()
+    # FP16-shifted storage on the 512^3 Taylor-Green workload: 108
+    # algorithmic bytes per LU (27 x 2 B read + written)
+    n5 = 512
+    g = make_lattice(elbm, "D3Q27", n5, "fp16_shifted", nu_for(n5))
+    g.set_diagnostics(diag_every=0)
+    g.step(2, "formula")
+    steps = 10
+    ms, kms, nk = time_steps(g, steps, "formula", stream)
+    g.close()
+    kernel_gbs = BYTES_PER_LU[("D3Q27", 2)] * n5 ** 3 * nk / (kms * 1e-3) / 1e9
+    out["d3q27_512_fp16_formula"] = round(n5 ** 3 * steps / (ms * 1e3), 1)
+    out["d3q27_512_fp16_roofline"] = {
+        "kernel": "k_sc16<D3Q27> (pipelined FP16-shifted FORMULA)",
+        "bytes_per_lu": BYTES_PER_LU[("D3Q27", 2)],
+        "achieved_gbs": round(kernel_gbs, 1),
+        "frac": round(kernel_gbs / peaks()[0], 4), "peak_kind": peaks()[1]}
     out["unit"] = "MLUPS"
     out["speedup_formula_vs_root_d3q27_fp32"] = round(
         out["d3q27_256_fp32_formula"] / out["d3q27_256_fp32_root"], 1)
@@ -354,7 +373,9 @@ def run_elbm(args):
     stream = torch.cuda.current_stream()
     n = args.n
     nu = nu_for(n)
-    g = make_lattice(elbm, "D3Q27", n, "fp32_shifted", nu)
+    fp16 = args.storage == "fp16_shifted"
+    esize = 2 if fp16 else 4
+    g = make_lattice(elbm, "D3Q27", n, args.storage, nu)
     g.set_diagnostics(diag_every=args.diag_every)
     g.step(args.warmup, "formula")
     g.sync()
@@ -371,13 +392,14 @@ def run_elbm(args):
     value = nodes * args.steps * world / (ms * 1e3)
     hbm, hbm_kind = peaks()
     kernel_ms = kms / max(nk, 1)
-    achieved = BYTES_PER_LU[("D3Q27", 4)] * nodes / (kernel_ms * 1e-3) / 1e9
+    achieved = BYTES_PER_LU[("D3Q27", esize)] * nodes / (kernel_ms * 1e-3) / 1e9
     # one checked step (untimed): violations and decision statistics
     g.set_diagnostics(diag_every=1, check_every=1)
     g.step(1, "formula")
     st = g.entropy_stats()
     result = {
-        "metric": "MLUPS (D3Q27 FORMULA FP32-shifted)",
+        "metric": "MLUPS (D3Q27 FORMULA %s)" % (
+            "FP16-shifted" if fp16 else "FP32-shifted"),
         "value": round(value, 1),
         "unit": "MLUPS",
         "n_gpus": world,
@@ -388,29 +410,35 @@ def run_elbm(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
+        "storage": "f16" if fp16 else "f32",
         "data": "synthetic",
         "config": {
             "workload": "D3Q27 periodic Taylor-Green vortex %d^3, Re=1600, "
-                        "u0=0.05, nu=%.4g, FP32 populations stored as "
-                        "f - W rho0, alpha FORMULA" % (n, nu),
+                        "u0=0.05, nu=%.4g, %s populations stored as "
+                        "f - W rho0, alpha FORMULA"
+                        % (n, nu, "FP16 (scaled by 2^k_i)" if fp16 else "FP32"),
             "nodes": nodes,
             "diag_every": args.diag_every,
             "l2": "inputs larger than L2 (%.1f GB of populations read per "
-                  "step vs 129 MB L2); no flush" % (nodes * 108 / 1e9),
+                  "step vs 129 MB L2); no flush" % (nodes * 27 * esize / 1e9),
             "parallelism": "replicas" if world > 1 else "single GPU",
         },
         "roofline": {
             "bound": "hbm",
-            "kernel": "k_sc32<D3Q27,shifted> (pipelined FP32 FORMULA stream-collide)",
+            "kernel": ("k_sc16<D3Q27> (pipelined FP16-shifted FORMULA "
+                       "stream-collide)" if fp16 else
+                       "k_sc32<D3Q27,shifted> (pipelined FP32 FORMULA "
+                       "stream-collide)"),
             "achieved": round(achieved, 1),
             "peak": hbm,
             "peak_kind": hbm_kind,
             "unit": "GB/s",
             "frac": round(achieved / hbm, 4),
-            "bytes_per_launch": BYTES_PER_LU[("D3Q27", 4)] * nodes,
+            "bytes_per_launch": BYTES_PER_LU[("D3Q27", esize)] * nodes,
             "kernel_ms": round(kernel_ms, 4),
             "traffic": (round(TRAFFIC_RECORD["bytes_per_node"] * nodes)
-                        if kernel_sha() == TRAFFIC_RECORD["sha"] else None),
+                        if not fp16 and kernel_sha() == TRAFFIC_RECORD["sha"]
+                        else None),
         },
         "gpu_launches": launches,
         "clocks": ck,
@@ -457,7 +485,7 @@ def e2e(elbm, args, n, nu, stream, world):
     del rho, u
     out_rho = torch.empty(rho_h.shape, dtype=torch.float64, pin_memory=True)
     out_u = torch.empty(u_h.shape, dtype=torch.float64, pin_memory=True)
-    g = elbm.Lattice("D3Q27", n, n, n, nu=nu, dtype="fp32_shifted")
+    g = elbm.Lattice("D3Q27", n, n, n, nu=nu, dtype=args.storage)
     g.set_diagnostics(diag_every=1)
     g.init_fields(rho_h.numpy(), u_h.numpy())     # allocate once, untimed
     g.step(args.warmup, "formula")
@@ -506,7 +534,8 @@ def run_reference(args):
     value = n ** 3 * args.steps / dt / 1e6
     print(json.dumps({
         "impl": "reference",
-        "metric": "MLUPS (D3Q27 FORMULA FP32-shifted)",
+        "metric": "MLUPS (D3Q27 FORMULA %s)" % (
+            "FP16-shifted" if fp16 else "FP32-shifted"),
         "value": round(value, 3), "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt * 1e3 / args.steps, 3),

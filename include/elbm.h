@@ -69,13 +69,21 @@ typedef enum { ELBM_D2Q9 = 0, ELBM_D3Q27 = 1 } elbm_lattice;
  *   ELBM_FP32          f_i in FP32.
  *   ELBM_FP32_SHIFTED  delta_i = f_i - W_i rho0 in FP32 (rho0 a per-handle
  *                      constant, the FP32-rounded mean initial density).
- * FP32 storages compute FORMULA in FP32 with a certified error bound on the
- * entropy differences (see elbm_step); ROOT and SECANT, and nodes far from
- * equilibrium, are computed in FP64 from the stored values. */
+ *   ELBM_FP16_SHIFTED  delta_i 2^k_i in IEEE binary16, k_i = round(log2(1/W_i))
+ *                      (D2Q9: 1, 3, 5; D3Q27: 2, 4, 6, 8 for 0..3 nonzero
+ *                      velocity components); the shift W_i rho0 stays a
+ *                      per-handle constant.  Each stored value is rounded
+ *                      to nearest once per step (relative 2^-11), so mass
+ *                      and momentum are conserved to that rounding only.
+ * FP32 and FP16 storages compute FORMULA in FP32 with a certified error bound
+ * on the entropy differences (see elbm_step) applied to the values as
+ * loaded; ROOT and SECANT, and nodes far from equilibrium, are computed in
+ * FP64 from the stored values. */
 typedef enum {
   ELBM_FP64 = 0,
   ELBM_FP32 = 1,
-  ELBM_FP32_SHIFTED = 2
+  ELBM_FP32_SHIFTED = 2,
+  ELBM_FP16_SHIFTED = 3
 } elbm_dtype;
 
 typedef enum {

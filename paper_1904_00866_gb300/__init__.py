@@ -24,10 +24,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libelbm.so")
 
 D2Q9, D3Q27 = 0, 1
-FP64, FP32, FP32_SHIFTED = 0, 1, 2
+FP64, FP32, FP32_SHIFTED, FP16_SHIFTED = 0, 1, 2, 3
 FORMULA, ROOT, SECANT = 0, 1, 2
 LATTICES = {"D2Q9": D2Q9, "D3Q27": D3Q27}
-DTYPES = {"fp64": FP64, "fp32": FP32, "fp32_shifted": FP32_SHIFTED}
+DTYPES = {"fp64": FP64, "fp32": FP32, "fp32_shifted": FP32_SHIFTED,
+          "fp16_shifted": FP16_SHIFTED}
 MODES = {"formula": FORMULA, "root": ROOT, "secant": SECANT}
 Q = {D2Q9: 9, D3Q27: 27}
 DIM = {D2Q9: 2, D3Q27: 3}
@@ -195,7 +196,8 @@ def _torch_cuda():
 class Lattice:
     """One periodic lattice advanced on the GPU.
 
-    lattice: "D2Q9" | "D3Q27"; dtype: "fp64" | "fp32" | "fp32_shifted";
+    lattice: "D2Q9" | "D3Q27"; dtype: "fp64" | "fp32" | "fp32_shifted" |
+    "fp16_shifted";
     allocator: "torch" (PyTorch caching allocator, the default when PyTorch
     sees a GPU) or "cuda" (cudaMalloc inside the library).
     """

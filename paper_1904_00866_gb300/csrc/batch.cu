@@ -433,6 +433,7 @@ static Geo member_geo(const BatchMember& mm) {
   g.ny = mm.ny;
   g.nz = mm.nz;
   g.n = mm.n;
+  g.ps = mm.n;
   g.rho0 = mm.rho0;
   g.shifted = 1;
   return g;

@@ -38,7 +38,16 @@ void stats_from_slots(const double* slots, double rho0, long long n,
                                          int* grid_used);                     \
   cudaError_t launch_fp64_##LAT(int mode, int diag, int check,               \
                                 const StepParams& p, int grid, int block,     \
-                                cudaStream_t s, int* grid_used);
+                                cudaStream_t s, int* grid_used);              \
+  cudaError_t launch_fp16_formula_##LAT(int diag, int check,                 \
+                                        const StepParams& p, int grid,        \
+                                        cudaStream_t s, int* grid_used);      \
+  cudaError_t launch_far16_##LAT(int diag, int check, const StepParams& p,   \
+                                 int grid, cudaStream_t s);                  \
+  cudaError_t launch_fp16_fp64mode_##LAT(int mode, int diag, int check,      \
+                                         const StepParams& p, int grid,       \
+                                         int block, cudaStream_t s,           \
+                                         int* grid_used);
 ELBM_DECLARE_LAUNCHERS(d2q9)
 ELBM_DECLARE_LAUNCHERS(d3q27)
 #undef ELBM_DECLARE_LAUNCHERS

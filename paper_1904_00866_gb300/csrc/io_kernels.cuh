@@ -1,9 +1,10 @@
 // Initialisation and readout kernels of the pull-layout storage (FP64,
-// FP32 or FP32-shifted populations), shared by the single-lattice runtime
-// and the batched runtime.
+// FP32, FP32-shifted or FP16-shifted populations), shared by the
+// single-lattice runtime and the batched runtime.
 #pragma once
 #include <math.h>
 
+#include "fp16_storage.cuh"
 #include "lattice.cuh"
 #include "node_fp64.cuh"
 
@@ -42,19 +43,36 @@ __device__ __forceinline__ void equilibrium_dev(double rho, const double* u,
   }
 }
 
-// Storage value of a population f whose deviation from W_i rho0 is dev.
-template <class T>
-__device__ __forceinline__ T to_storage(double f, double dev, int shifted) {
-  if (sizeof(T) == 8) return (T)f;
-  return shifted ? (T)dev : (T)f;
-}
-
 struct Geo {
   int nx, ny, nz;
   long long n;
+  long long ps;  // population stride (elements)
   double rho0;
-  int shifted;   // FP32_SHIFTED storage
+  int shifted;   // FP32_SHIFTED storage (FP16 storage is always shifted)
 };
+
+// Storage value of population i, f, whose deviation from W_i rho0 is dev.
+template <class L, class T>
+__device__ __forceinline__ T to_storage(const Geo& g, int i, double f,
+                                        double dev) {
+  if constexpr (sizeof(T) == 8)
+    return (T)f;
+  else if constexpr (sizeof(T) == 4)
+    return g.shifted ? (T)dev : (T)f;
+  else
+    return h16_from_dev<L>(dev, i);
+}
+
+// Population i from its storage value.
+template <class L, class T>
+__device__ __forceinline__ double from_storage(const Geo& g, int i, T v) {
+  if constexpr (sizeof(T) == 8)
+    return v;
+  else if constexpr (sizeof(T) == 4)
+    return g.shifted ? L::w(i) * g.rho0 + (double)v : (double)v;
+  else
+    return h16_to_f<L>(v, i, g.rho0);
+}
 
 template <class L>
 __device__ __forceinline__ long long shifted_node(const Geo& g, long long node,
@@ -94,8 +112,8 @@ __global__ void k_init_feq(Geo g, const double* __restrict__ rho,
     equilibrium_dev<L>(bad ? 1.0 : r, uu, g.rho0, dev, fe);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i)
-      f[i * g.n + shifted_node<L>(g, node, i, -1)] =
-          to_storage<T>(fe[i], dev[i], g.shifted);
+      f[i * g.ps + shifted_node<L>(g, node, i, -1)] =
+          to_storage<L, T>(g, i, fe[i], dev[i]);
   }
 }
 
@@ -109,8 +127,8 @@ __global__ void k_set_pop(Geo g, const double* __restrict__ fin, void* fv) {
     for (int i = 0; i < L::Q; ++i) {
       const double v = fin[i * g.n + node];
       const double s = L::w(i) * g.rho0;
-      f[i * g.n + shifted_node<L>(g, node, i, -1)] =
-          to_storage<T>(v, v - s, g.shifted);
+      f[i * g.ps + shifted_node<L>(g, node, i, -1)] =
+          to_storage<L, T>(g, i, v, v - s);
     }
   }
 }
@@ -118,9 +136,7 @@ __global__ void k_set_pop(Geo g, const double* __restrict__ fin, void* fv) {
 template <class L, class T>
 __device__ __forceinline__ double load_pre(const Geo& g, const T* f,
                                            long long node, int i) {
-  const double v = (double)f[i * g.n + shifted_node<L>(g, node, i, -1)];
-  if (sizeof(T) == 4 && g.shifted) return L::w(i) * g.rho0 + v;
-  return v;
+  return from_storage<L, T>(g, i, f[i * g.ps + shifted_node<L>(g, node, i, -1)]);
 }
 
 // Storage -> pre-collision populations / moments (gather).

@@ -30,6 +30,15 @@ struct D2Q9 {
   __host__ __device__ static constexpr int nonzero(int i) {
     return (c(i, 0) != 0) + (c(i, 1) != 0) + (c(i, 2) != 0);
   }
+  // binary16 storage scale 2^k_i, k_i = round(log2(1 / W_i)): the stored
+  // value is (f_i - W_i rho0) 2^k_i, so every population class uses the
+  // same part of the binary16 range; powers of two scale exactly
+  __host__ __device__ static constexpr float hscale(int i) {
+    return nonzero(i) == 0 ? 2.0f : (nonzero(i) == 1 ? 8.0f : 32.0f);
+  }
+  __host__ __device__ static constexpr float hscale_inv(int i) {
+    return nonzero(i) == 0 ? 0.5f : (nonzero(i) == 1 ? 0.125f : 0.03125f);
+  }
 };
 
 struct D3Q27 {
@@ -62,5 +71,17 @@ struct D3Q27 {
   }
   __host__ __device__ static constexpr int nonzero(int i) {
     return (c(i, 0) != 0) + (c(i, 1) != 0) + (c(i, 2) != 0);
+  }
+  // binary16 storage scale 2^k_i, k_i = round(log2(1 / W_i))
+  __host__ __device__ static constexpr float hscale(int i) {
+    return nonzero(i) == 0
+               ? 4.0f
+               : (nonzero(i) == 1 ? 16.0f : (nonzero(i) == 2 ? 64.0f : 256.0f));
+  }
+  __host__ __device__ static constexpr float hscale_inv(int i) {
+    return nonzero(i) == 0
+               ? 0.25f
+               : (nonzero(i) == 1 ? 0.0625f
+                                  : (nonzero(i) == 2 ? 0.015625f : 0.00390625f));
   }
 };

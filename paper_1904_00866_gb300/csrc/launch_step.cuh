@@ -2,6 +2,7 @@
 // instantiates the subset it owns so the kernels compile in parallel.
 #pragma once
 #include "internal.h"
+#include "sc16.cuh"
 #include "sc32.cuh"
 #include "sc32_tma.cuh"
 
@@ -152,19 +153,59 @@ static cudaError_t launch_sc32(int diag, int check, const StepParams& p,
   return launch_sc32_s<L, true>(diag, check, p, grid, s, grid_used);
 }
 
-// The fixup grid must equal the grid of the FP32 step when DIAG is set (its
-// partials rows follow the step's rows); without DIAG any grid works.
+// Pipelined FP16-shifted FORMULA kernel (dynamic shared memory: 2 stages x
+// Q x 256 words).
+template <class L, int DIAG, int CHECK>
+static cudaError_t launch_sc16_one(const StepParams& p, int grid,
+                                   cudaStream_t s, int* grid_used) {
+  auto k = k_sc16<L, DIAG, CHECK>;
+  const int smem = 2 * L::Q * kSc32Threads * (int)sizeof(unsigned);
+  static bool configured = false;   // per instantiation
+  if (!configured) {
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    configured = true;
+  }
+  if (grid <= 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kSc32Threads,
+                                                  smem);
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 2048 / kSc32Threads) per_sm = 2048 / kSc32Threads;
+    long long g = (long long)sms * per_sm;
+    const long long tiles = (p.n + kSc32Threads - 1) / kSc32Threads;
+    if (tiles < g) g = tiles;
+    grid = g < 1 ? 1 : (int)g;
+  }
+  if (grid_used) *grid_used = grid;
+  k<<<grid, kSc32Threads, smem, s>>>(p);
+  count_launch();
+  return cudaGetLastError();
+}
+
 template <class L>
+static cudaError_t launch_sc16(int diag, int check, const StepParams& p,
+                               int grid, cudaStream_t s, int* grid_used) {
+  if (check) return launch_sc16_one<L, 1, 1>(p, grid, s, grid_used);
+  if (diag) return launch_sc16_one<L, 1, 0>(p, grid, s, grid_used);
+  return launch_sc16_one<L, 0, 0>(p, grid, s, grid_used);
+}
+
+// The fixup grid must equal the grid of the FP32 / FP16 step when DIAG is
+// set (its partials rows follow the step's rows); without DIAG any grid
+// works.  S: storage type (float or half_t).
+template <class L, class S = float>
 static cudaError_t launch_far_lattice(int diag, int check,
                                       const StepParams& p, int grid,
                                       cudaStream_t s) {
   if (grid <= 0) grid = 152;
   if (check)
-    k_far_fixup<L, 1, 1><<<grid, 256, 0, s>>>(p);
+    k_far_fixup<L, S, 1, 1><<<grid, 256, 0, s>>>(p);
   else if (diag)
-    k_far_fixup<L, 1, 0><<<grid, 256, 0, s>>>(p);
+    k_far_fixup<L, S, 1, 0><<<grid, 256, 0, s>>>(p);
   else
-    k_far_fixup<L, 0, 0><<<grid, 256, 0, s>>>(p);
+    k_far_fixup<L, S, 0, 0><<<grid, 256, 0, s>>>(p);
   count_launch();
   return cudaGetLastError();
 }

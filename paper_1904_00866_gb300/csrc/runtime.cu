@@ -147,7 +147,14 @@ namespace elbm {
 void set_global_error(const std::string& msg) { g_create_err = msg; }
 }  // namespace elbm
 
-static size_t elem_size(elbm_dtype t) { return t == ELBM_FP64 ? 8 : 4; }
+static size_t elem_size(elbm_dtype t) {
+  return t == ELBM_FP64 ? 8 : (t == ELBM_FP16_SHIFTED ? 2 : 4);
+}
+
+// Population stride of the storage arrays (elements).
+static long long pop_stride(const elbm_handle* h) {
+  return h->dtype == ELBM_FP16_SHIFTED ? fp16_pop_stride(h->n) : h->n;
+}
 
 static elbm_status fail(elbm_handle* h, elbm_status st, const std::string& m) {
   if (h)
@@ -201,7 +208,7 @@ static int max_grid_rows() {
 
 static elbm_status ensure_buffers(elbm_handle* h) {
   if (h->allocated) return ELBM_OK;
-  const size_t fb = (size_t)h->q * h->n * elem_size(h->dtype);
+  const size_t fb = (size_t)h->q * pop_stride(h) * elem_size(h->dtype);
   h->f[0] = dev_alloc(h, fb);
   h->f[1] = dev_alloc(h, fb);
   h->partial_rows_max = 2 * max_grid_rows();
@@ -235,8 +242,9 @@ static Geo geo(const elbm_handle* h) {
   g.ny = h->ny;
   g.nz = h->nz;
   g.n = h->n;
+  g.ps = pop_stride(h);
   g.rho0 = h->dtype == ELBM_FP64 ? 0.0 : h->rho0;
-  g.shifted = h->dtype == ELBM_FP32_SHIFTED;
+  g.shifted = h->dtype == ELBM_FP32_SHIFTED || h->dtype == ELBM_FP16_SHIFTED;
   return g;
 }
 
@@ -253,11 +261,15 @@ static int grid_for(long long n) {
     if ((h)->lattice == ELBM_D2Q9) {                                         \
       if ((h)->dtype == ELBM_FP64)                                           \
         KERNEL<D2Q9, double><<<grid_, 256, 0, (h)->stream>>>(__VA_ARGS__);   \
+      else if ((h)->dtype == ELBM_FP16_SHIFTED)                              \
+        KERNEL<D2Q9, half_t><<<grid_, 256, 0, (h)->stream>>>(__VA_ARGS__);   \
       else                                                                   \
         KERNEL<D2Q9, float><<<grid_, 256, 0, (h)->stream>>>(__VA_ARGS__);    \
     } else {                                                                 \
       if ((h)->dtype == ELBM_FP64)                                           \
         KERNEL<D3Q27, double><<<grid_, 256, 0, (h)->stream>>>(__VA_ARGS__);  \
+      else if ((h)->dtype == ELBM_FP16_SHIFTED)                              \
+        KERNEL<D3Q27, half_t><<<grid_, 256, 0, (h)->stream>>>(__VA_ARGS__);  \
       else                                                                   \
         KERNEL<D3Q27, float><<<grid_, 256, 0, (h)->stream>>>(__VA_ARGS__);   \
     }                                                                        \
@@ -290,7 +302,8 @@ elbm_status elbm_create(elbm_handle** out, elbm_lattice lattice, int nx,
   *out = nullptr;
   if (lattice != ELBM_D2Q9 && lattice != ELBM_D3Q27)
     return fail(nullptr, ELBM_EINVAL, "unknown lattice");
-  if (dtype != ELBM_FP64 && dtype != ELBM_FP32 && dtype != ELBM_FP32_SHIFTED)
+  if (dtype != ELBM_FP64 && dtype != ELBM_FP32 && dtype != ELBM_FP32_SHIFTED &&
+      dtype != ELBM_FP16_SHIFTED)
     return fail(nullptr, ELBM_EINVAL, "unknown dtype");
   if (nx < 1 || ny < 1 || nz < 1)
     return fail(nullptr, ELBM_EINVAL, "lattice dimensions must be >= 1");
@@ -492,6 +505,7 @@ elbm_status elbm_step(elbm_handle* h, long long nsteps, elbm_alpha_mode mode) {
   p.ny = h->ny;
   p.nz = h->nz;
   p.n = h->n;
+  p.ps = pop_stride(h);
   p.chunks = (h->nx + 31) / 32;
   p.tiles = (long long)p.chunks * h->ny * h->nz;
   p.beta = h->beta;
@@ -521,7 +535,10 @@ elbm_status elbm_step(elbm_handle* h, long long nsteps, elbm_alpha_mode mode) {
   if (nsteps > 0) cudaMemsetAsync(h->far_count, 0, 2 * sizeof(unsigned),
                                   h->stream);
   const bool d2 = h->lattice == ELBM_D2Q9;
-  const int storage = h->dtype == ELBM_FP64 ? 0 : 1;
+  // 0: FP64, 1: FP32 (shifted or not), 2: FP16-shifted
+  const int storage =
+      h->dtype == ELBM_FP64 ? 0 : (h->dtype == ELBM_FP16_SHIFTED ? 2 : 1);
+  const size_t esz = elem_size(h->dtype);
   for (long long s = 0; s < nsteps; ++s) {
     const long long n = h->step;
     const int check = h->check_every > 0 && n % h->check_every == 0;
@@ -529,17 +546,18 @@ elbm_status elbm_step(elbm_handle* h, long long nsteps, elbm_alpha_mode mode) {
     const bool amap = h->amap_every > 0 && n % h->amap_every == 0;
     p.f_in = h->f[h->cur];
     p.f_out = h->f[h->cur ^ 1];
-    if (storage == 1) {
+    if (storage != 0) {
       for (int i = 0; i < h->q; ++i) {
-        p.in_pop[i] = (const float*)p.f_in + (size_t)i * h->n;
-        p.out_pop[i] = (float*)p.f_out + (size_t)i * h->n;
+        p.in_pop[i] = (const float*)((const char*)p.f_in +
+                                     (size_t)i * p.ps * esz);
+        p.out_pop[i] = (float*)((char*)p.f_out + (size_t)i * p.ps * esz);
       }
     }
     p.alpha_map = amap ? h->alpha_map : nullptr;
     p.parity = (int)(n & 1);
     int grid = 0;
     cudaError_t e;
-    const bool fp32_formula = storage == 1 && mode == ELBM_ALPHA_FORMULA;
+    const bool fp32_formula = storage != 0 && mode == ELBM_ALPHA_FORMULA;
     std::pair<cudaEvent_t, cudaEvent_t>* ev = nullptr;
     if (h->profiling) {
       if (h->events_used == h->events.size()) {
@@ -554,10 +572,18 @@ elbm_status elbm_step(elbm_handle* h, long long nsteps, elbm_alpha_mode mode) {
     if (storage == 0)
       e = d2 ? launch_fp64_d2q9(mode, diag, check, p, 0, 256, h->stream, &grid)
              : launch_fp64_d3q27(mode, diag, check, p, 0, 256, h->stream, &grid);
+    else if (fp32_formula && storage == 2)
+      e = d2 ? launch_fp16_formula_d2q9(diag, check, p, 0, h->stream, &grid)
+             : launch_fp16_formula_d3q27(diag, check, p, 0, h->stream, &grid);
     else if (fp32_formula)
       e = d2 ? launch_fp32_formula_d2q9(diag, check, p, 0, 256, h->stream, &grid)
              : launch_fp32_formula_d3q27(diag, check, p, 0, 256, h->stream,
                                          &grid);
+    else if (storage == 2)
+      e = d2 ? launch_fp16_fp64mode_d2q9(mode, diag, check, p, 0, 256,
+                                         h->stream, &grid)
+             : launch_fp16_fp64mode_d3q27(mode, diag, check, p, 0, 256,
+                                          h->stream, &grid);
     else
       e = d2 ? launch_fp32_fp64mode_d2q9(mode, diag, check, p, 0, 256,
                                          h->stream, &grid)
@@ -570,8 +596,12 @@ elbm_status elbm_step(elbm_handle* h, long long nsteps, elbm_alpha_mode mode) {
       StepParams pf = p;
       pf.partials = h->partials + (size_t)grid * NSTAT;
       const int fgrid = grid < 152 ? grid : 152;
-      e = d2 ? launch_far_d2q9(diag, check, pf, fgrid, h->stream)
-             : launch_far_d3q27(diag, check, pf, fgrid, h->stream);
+      if (storage == 2)
+        e = d2 ? launch_far16_d2q9(diag, check, pf, fgrid, h->stream)
+               : launch_far16_d3q27(diag, check, pf, fgrid, h->stream);
+      else
+        e = d2 ? launch_far_d2q9(diag, check, pf, fgrid, h->stream)
+               : launch_far_d3q27(diag, check, pf, fgrid, h->stream);
       if (e != cudaSuccess) return cuda_fail(h, e, "far fixup launch");
       rows += fgrid;
     }

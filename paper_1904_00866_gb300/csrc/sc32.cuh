@@ -64,6 +64,33 @@ struct Acc32 {
   }
 };
 
+// Block reduction of the per-thread FP32 accumulators into one partials
+// row (FP64 slots).
+__device__ __forceinline__ void store_acc32(const Acc32& acc,
+                                            double* partials) {
+  Acc a;
+  a.init();
+  a.drho = acc.drho.value();
+  a.j0 = acc.j0.value();
+  a.j1 = acc.j1.value();
+  a.j2 = acc.j2.value();
+  a.ke = acc.ke.value();
+  a.asum = acc.asum.value();
+  a.h = acc.h;
+  a.amin = acc.amin;
+  a.amax = acc.amax;
+  a.adev = acc.adev;
+  a.nodes = acc.nodes;
+  a.acc2 = acc.acc2;
+  a.accstar = acc.acc2;
+  a.formula = acc.formula;
+  a.band = acc.band;
+  a.degen = acc.degen;
+  a.viol = acc.viol;
+  a.mismatch = acc.mismatch;
+  a.block_reduce_store(partials);
+}
+
 template <class L>
 __device__ __forceinline__ void node_xyz(const StepParams& p, unsigned node,
                                          int& x, int& y, int& z) {
@@ -218,29 +245,7 @@ __global__ void __launch_bounds__(kSc32Threads, 2)
     }
   }
   cp_async_wait<0>();
-  if (DIAG) {
-    Acc a;
-    a.init();
-    a.drho = acc.drho.value();
-    a.j0 = acc.j0.value();
-    a.j1 = acc.j1.value();
-    a.j2 = acc.j2.value();
-    a.ke = acc.ke.value();
-    a.asum = acc.asum.value();
-    a.h = acc.h;
-    a.amin = acc.amin;
-    a.amax = acc.amax;
-    a.adev = acc.adev;
-    a.nodes = acc.nodes;
-    a.acc2 = acc.acc2;
-    a.accstar = acc.acc2;
-    a.formula = acc.formula;
-    a.band = acc.band;
-    a.degen = acc.degen;
-    a.viol = acc.viol;
-    a.mismatch = acc.mismatch;
-    a.block_reduce_store(p.partials);
-  }
+  if (DIAG) store_acc32(acc, p.partials);
 }
 
 }  // namespace elbm

@@ -199,29 +199,7 @@ __global__ void __launch_bounds__(256, 2) k_sc32_tma(const StepParams p) {
     // too, so they get there as well)
     for (int st = 0; st < S; ++st) mbar_wait_bounded(&full[st], 0u);
   }
-  if (DIAG) {
-    Acc a;
-    a.init();
-    a.drho = acc.drho.value();
-    a.j0 = acc.j0.value();
-    a.j1 = acc.j1.value();
-    a.j2 = acc.j2.value();
-    a.ke = acc.ke.value();
-    a.asum = acc.asum.value();
-    a.h = acc.h;
-    a.amin = acc.amin;
-    a.amax = acc.amax;
-    a.adev = acc.adev;
-    a.nodes = acc.nodes;
-    a.acc2 = acc.acc2;
-    a.accstar = acc.acc2;
-    a.formula = acc.formula;
-    a.band = acc.band;
-    a.degen = acc.degen;
-    a.viol = acc.viol;
-    a.mismatch = acc.mismatch;
-    a.block_reduce_store(p.partials);
-  }
+  if (DIAG) store_acc32(acc, p.partials);
 }
 
 }  // namespace elbm

@@ -122,6 +122,7 @@ extern "C" elbm_status elbm_step_static(
   p.ny = ny;
   p.nz = nz;
   p.n = n;
+  p.ps = n;
   p.chunks = (nx + 31) / 32;
   p.tiles = (long long)p.chunks * ny * nz;
   const double cs2 = 1.0 / 3.0;

@@ -12,12 +12,14 @@
 // +-1 x-shift of a row is absorbed by L1/L2.
 //
 // Template parameters: lattice L, storage type T (double: FP64 arithmetic
-// for every alpha mode; float: FP32 storage with ROOT / SECANT in FP64 --
-// FP32 FORMULA runs in the pipelined k_sc32), alpha MODE, DIAG (fused
-// statistics), CHECK (FP64 entropy check; implies DIAG).
+// for every alpha mode; float / half_t: FP32 or FP16-shifted storage with
+// ROOT / SECANT in FP64 -- their FORMULA runs in the pipelined k_sc32 /
+// k_sc16), alpha MODE, DIAG (fused statistics), CHECK (FP64 entropy check;
+// implies DIAG).
 #pragma once
 #include <stdint.h>
 
+#include "fp16_storage.cuh"
 #include "lattice.cuh"
 #include "node_fp64.cuh"
 #include "stats.cuh"
@@ -54,6 +56,8 @@ struct StepParams {
   int nx, ny, nz;
   int chunks;             // ceil(nx / 32)
   long long n;            // nodes
+  long long ps;           // population stride in elements (n, or n padded
+                          // to a multiple of 64 for FP16 storage)
   long long tiles;        // chunks * ny * nz
   double beta;
   double rho0;            // shift reference (0 for FP64 storage)
@@ -66,8 +70,10 @@ struct StepParams {
   unsigned far_cap;       // capacity of far_queue (entries)
   int parity;             // step parity selecting far_count[parity]
   FastDiv div_nx, div_ny; // node -> (x, y, z)
-  const float* in_pop[27];  // FP32 storage: f_in + i n, per population
-  float* out_pop[27];       // FP32 storage: f_out + i n
+  // FP32 / FP16 storage: f_in + i ps and f_out + i ps, per population (for
+  // FP16 the pointers address binary16 arrays; the kernels cast them)
+  const float* in_pop[27];
+  float* out_pop[27];
 };
 
 template <class L>
@@ -145,13 +151,13 @@ __global__ void __launch_bounds__(256)
 
     T v[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) v[i] = fin[(long long)i * p.n + src_index<L>(p, i, x, y, z)];
+    for (int i = 0; i < Q; ++i) v[i] = fin[(long long)i * p.ps + src_index<L>(p, i, x, y, z)];
 
     auto store_T = [&](int i, double val) {
       if (i < 0) {
         p.alpha_map[node] = (float)val;
       } else {
-        fout[(long long)i * p.n + node] = (T)val;
+        fout[(long long)i * p.ps + node] = (T)val;
       }
     };
 
@@ -167,34 +173,38 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         const double s = L::w(i) * p.rho0;
-        nd.f[i] = p.unshifted ? (double)v[i] : s + (double)v[i];
+        if constexpr (sizeof(T) == 2)
+          nd.f[i] = h16_to_f<L>(v[i], i, p.rho0);
+        else
+          nd.f[i] = p.unshifted ? (double)v[i] : s + (double)v[i];
       }
       auto store_s = [&](int i, double val) {
         if (i < 0) {
           p.alpha_map[node] = (float)val;
         } else {
           const double s = L::w(i) * p.rho0;
-          fout[(long long)i * p.n + node] =
-              (T)(p.unshifted ? val : val - s);
+          if constexpr (sizeof(T) == 2)
+            fout[(long long)i * p.ps + node] = h16_from_dev<L>(val - s, i);
+          else
+            fout[(long long)i * p.ps + node] =
+                (T)(p.unshifted ? val : val - s);
         }
       };
       collide64<L, MODE, CHECK>(nd, p, true, acc, DIAG != 0, store_s);
     } else {
       static_assert(sizeof(T) == 8 || MODE != MODE_FORMULA,
-                    "FP32 FORMULA runs in k_sc32");
+                    "FP32 / FP16 FORMULA runs in k_sc32 / k_sc16");
     }
   }
   if (DIAG) acc.block_reduce_store(p.partials);
 }
 
-// FP64 collision of the nodes the FP32 FORMULA kernel deferred.  Resets
-// the other parity's counter for the next step (stream order makes that
-// counter idle here).
-template <class L, int DIAG, int CHECK>
+// FP64 collision of the nodes the FP32 / FP16 FORMULA kernel deferred (S:
+// the storage type, float or half_t).  Resets the other parity's counter
+// for the next step (stream order makes that counter idle here).
+template <class L, class S, int DIAG, int CHECK>
 __global__ void __launch_bounds__(256) k_far_fixup(const StepParams p) {
   constexpr int Q = L::Q;
-  const float* __restrict__ fin = static_cast<const float*>(p.f_in);
-  float* __restrict__ fout = static_cast<float*>(p.f_out);
   const unsigned count = min(p.far_count[p.parity], p.far_cap);
   Acc acc;
   acc.init();
@@ -207,14 +217,23 @@ __global__ void __launch_bounds__(256) k_far_fixup(const StepParams p) {
     Node64<L> nd;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const double v = (double)fin[(long long)i * p.n + src_index<L>(p, i, x, y, z)];
-      nd.f[i] = p.unshifted ? v : L::w(i) * p.rho0 + v;
+      const long long src = src_index<L>(p, i, x, y, z);
+      if constexpr (sizeof(S) == 2) {
+        nd.f[i] = h16_to_f<L>(
+            reinterpret_cast<const half_t*>(p.in_pop[i])[src], i, p.rho0);
+      } else {
+        const double v = (double)p.in_pop[i][src];
+        nd.f[i] = p.unshifted ? v : L::w(i) * p.rho0 + v;
+      }
     }
     auto store_s = [&](int i, double val) {
       if (i < 0) {
         p.alpha_map[node] = (float)val;
+      } else if constexpr (sizeof(S) == 2) {
+        reinterpret_cast<half_t*>(p.out_pop[i])[node] =
+            h16_from_dev<L>(val - L::w(i) * p.rho0, i);
       } else {
-        fout[(long long)i * p.n + node] =
+        p.out_pop[i][node] =
             (float)(p.unshifted ? val : val - L::w(i) * p.rho0);
       }
     };
