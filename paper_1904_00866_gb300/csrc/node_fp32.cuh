@@ -32,6 +32,11 @@
 //   else (node within FP32 noise of equilibrium) -> alpha = 1, for which
 //                              H(f*) = H(f^eq) <= H(f) holds exactly.
 // When |Delta H(2)| <= e2 the decision is flagged NF_BAND.
+//
+// Opposite-velocity populations are processed in pairs with packed f32x2
+// arithmetic (see npairs below); every lane operation rounds like its
+// scalar form, so only the order of the moment sums differs from a scalar
+// loop, which the summation error term of the bounds covers.
 #pragma once
 #include <math.h>
 
@@ -40,10 +45,41 @@
 
 namespace elbm {
 
+// Populations 2k-1 and 2k (k = 1..P, P = (Q - 1) / 2) have opposite
+// velocities.  Their values travel together as the two lanes of a float2,
+// so the per-population arithmetic issues as packed f32x2 instructions: one
+// issue slot for two IEEE operations, each lane rounded exactly like the
+// scalar operation.  Lane x holds population 2k-1 (velocity c), lane y
+// population 2k (velocity -c); population 0 (rest) stays scalar.
+template <class L>
+__host__ __device__ constexpr int npairs() {
+  return (L::Q - 1) / 2;
+}
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  return __fadd2_rn(a, b);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  return __fmul2_rn(a, b);
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  return __ffma2_rn(a, b, c);
+}
+// a - b rounded once (the product with -1 is exact)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+// lane signs (s, -s) of a velocity component s of lane x
+__device__ __forceinline__ float2 lane_sign(int s) {
+  return make_float2((float)s, (float)-s);
+}
+
 // Per-node result of the FP32 FORMULA evaluation.
 template <class L>
 struct N32 {
-  float n[L::Q];   // f^eq_i - f_i (not yet projected)
+  float n0;                    // f^eq_0 - f_0 (not yet projected)
+  float2 n2[npairs<L>()];      // the same for the pairs
   float alpha;
   unsigned flags;
   float drho, rho;
@@ -58,6 +94,9 @@ __device__ __forceinline__ float rcp_approx(float y) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y));
   return r;
 }
+__device__ __forceinline__ float2 rcp_approx2(float2 y) {
+  return make_float2(rcp_approx(y.x), rcp_approx(y.y));
+}
 
 // Index 0..3 of the distinct weight of population i (number of nonzero
 // velocity components).
@@ -66,62 +105,63 @@ __host__ __device__ constexpr int wclass(int i) {
   return L::nonzero(i);
 }
 
-// Mass/momentum of delta: rho-part and the three momentum components, from
-// per-(cy, cz) column sums (53 additions for D3Q27, 14 for D2Q9).
-template <class L, class Get>
-__device__ __forceinline__ void moment_sums(Get get, float& m0, float& mx,
-                                            float& my, float& mz) {
-  float A[3][3], B[3][3];
+// Mass and momentum sums m0 = sum_i v_i, m_a = sum_i c_ia v_i of a set
+// given as the rest value v0 and the pairs vv[k] (each lane accumulates
+// its own population's terms; 40 packed and 5 scalar operations for
+// D3Q27, 10 and 4 for D2Q9).
+template <class L>
+__device__ __forceinline__ void moments2(float v0,
+                                         const float2 (&vv)[npairs<L>()],
+                                         float& m0, float& mx, float& my,
+                                         float& mz) {
+  constexpr int P = npairs<L>();
+  float2 s = vv[0];
+  float2 acc[3] = {f2(0.0f), f2(0.0f), f2(0.0f)};
+  bool started[3] = {false, false, false};
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+  for (int k = 0; k < P; ++k) {
+    const int i = 2 * k + 1;
+    if (k > 0) s = add2(s, vv[k]);
 #pragma unroll
-    for (int b = 0; b < 3; ++b) A[a][b] = B[a][b] = 0.0f;
-#pragma unroll
-  for (int i = 0; i < L::Q; ++i) {
-    const float v = get(i);
-    const int cx = L::c(i, 0), cy = cidx(L::c(i, 1)), cz = cidx(L::c(i, 2));
-    A[cy][cz] += v;
-    if (cx == 1) B[cy][cz] += v;
-    if (cx == -1) B[cy][cz] -= v;
-  }
-  float s0 = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      s0 += A[a][b];
-      sx += B[a][b];
+    for (int a = 0; a < L::D; ++a) {
+      const int c = L::c(i, a);
+      if (c == 0) continue;
+      acc[a] = started[a] ? fma2(lane_sign(c), vv[k], acc[a])
+                          : mul2(lane_sign(c), vv[k]);
+      started[a] = true;
     }
-#pragma unroll
-  for (int b = 0; b < 3; ++b) sy += A[2][b] - A[0][b];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) sz += A[a][2] - A[a][0];
-  m0 = s0;
-  mx = sx;
-  my = sy;
-  mz = sz;
+  }
+  m0 = v0 + (s.x + s.y);
+  mx = acc[0].x + acc[0].y;
+  my = acc[1].x + acc[1].y;
+  mz = L::D == 3 ? acc[2].x + acc[2].y : 0.0f;
 }
 
-// d[i]: FP32 deviation delta_i (registers).  corr_rho / corr: used only for
-// plain FP32 storage (delta_i = v_i - s_i, s_i = fl(W_i rho0)), where
-// corr_rho = sum_i s_i - rho0 and corr_i = W_i rho0 - s_i.
+// d0, dd: FP32 deviations delta_i of the rest population and the pairs
+// (registers).  corr_rho / corr: used only for plain FP32 storage
+// (delta_i = v_i - s_i, s_i = fl(W_i rho0)), where corr_rho = sum_i s_i -
+// rho0 and corr_i = W_i rho0 - s_i.
 template <class L, bool SHIFTED>
-__device__ __forceinline__ void node32_formula(const float (&d)[L::Q],
-                                               float rho0, float corr_rho,
-                                               const float* __restrict__ corr,
-                                               float a_extra, N32<L>& r) {
+__device__ __forceinline__ void node32_formula(
+    float d0, const float2 (&dd)[npairs<L>()], float rho0, float corr_rho,
+    const float* __restrict__ corr, float a_extra, N32<L>& r) {
   constexpr int Q = L::Q;
+  constexpr int P = npairs<L>();
   constexpr float uu = 5.9604645e-8f;  // 2^-24
   r.flags = 0;
   r.alpha = 2.0f;
 
   // ---- exact mass and momentum: delta = hi + lo, hi on a 2^-20 grid ------
-  float hi[Q];
+  const float hi0 = (d0 + 12.0f) - 12.0f;
+  float2 hi[P], lo[P];
 #pragma unroll
-  for (int i = 0; i < Q; ++i) hi[i] = (d[i] + 12.0f) - 12.0f;
+  for (int k = 0; k < P; ++k) {
+    hi[k] = add2(add2(dd[k], f2(12.0f)), f2(-12.0f));
+    lo[k] = sub2(dd[k], hi[k]);
+  }
   float h0, hx, hy, hz, l0, lx, ly, lz;
-  moment_sums<L>([&](int i) { return hi[i]; }, h0, hx, hy, hz);
-  moment_sums<L>([&](int i) { return d[i] - hi[i]; }, l0, lx, ly, lz);
+  moments2<L>(hi0, hi, h0, hx, hy, hz);
+  moments2<L>(d0 - hi0, lo, l0, lx, ly, lz);
   float drho = h0 + l0;
   if (!SHIFTED) drho += corr_rho;
   const float j[3] = {hx + lx, hy + ly, hz + lz};
@@ -138,7 +178,7 @@ __device__ __forceinline__ void node32_formula(const float (&d)[L::Q],
   const float inv_rho = rcp_approx(rho);
 
   // ---- per-axis equilibrium factors -------------------------------------
-  float dp[3], dm[3], d0[3];
+  float dp[3], dm[3], dz[3];
   float U = 0.0f;
 #pragma unroll
   for (int a = 0; a < L::D; ++a) {
@@ -147,21 +187,26 @@ __device__ __forceinline__ void node32_formula(const float (&d)[L::Q],
     const float s = 3.0f * u * u / (1.0f + sqrtf(fmaf(3.0f * u, u, 1.0f)));
     dp[a] = fmaf(3.0f, u, 2.0f * s);
     dm[a] = fmaf(-3.0f, u, 2.0f * s);
-    d0[a] = -s;
+    dz[a] = -s;
   }
   if (!(U < 0.5f)) {
     r.flags = NF_FAR;
     return;
   }
-  // two-axis products (1 + a)(1 + b) - 1, shared by the z-columns
-  float pxy[3][3];
+  // factor pairs: lane x takes d(c), lane y takes d(-c)
+  auto fac = [&](int a, int c) {
+    return c == 1 ? make_float2(dp[a], dm[a])
+                  : (c == -1 ? make_float2(dm[a], dp[a]) : f2(dz[a]));
+  };
+  // two-axis products (1 + a)(1 + b) - 1 for lane-x velocities (cx, cy);
+  // entries no pair uses are never evaluated
+  float2 pxy[3][3];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      const float da = a == 2 ? dp[0] : (a == 0 ? dm[0] : d0[0]);
-      const float db = b == 2 ? dp[1] : (b == 0 ? dm[1] : d0[1]);
-      pxy[a][b] = fmaf(da, db, da + db);
+      const float2 da = fac(0, a - 1), db = fac(1, b - 1);
+      pxy[a][b] = fma2(da, db, add2(da, db));
     }
 
   // ---- n_i, x_i and the moments M_2..M_4 ---------------------------------
@@ -176,29 +221,52 @@ __device__ __forceinline__ void node32_formula(const float (&d)[L::Q],
     wd[k] = wk * drho;
     w0[k] = wk * rho0;
   }
-  float M2 = 0.f, M3 = 0.f, M4 = 0.f;
-  float xabs = 0.0f;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
-    float pm1 = pxy[cidx(cx)][cidx(cy)];
-    if (L::D == 3) {
-      const float a2 = cz == 1 ? dp[2] : (cz == -1 ? dm[2] : d0[2]);
-      pm1 = fmaf(pm1, a2, pm1 + a2);
-    }
-    const int k = wclass<L>(i);
-    float deq = fmaf(wr[k], pm1, wd[k]);      // W (drho + rho (P - 1))
-    if (!SHIFTED) deq += corr[i];
-    const float ni = deq - d[i];
-    r.n[i] = ni;
-    const float x = ni * rcp_approx(w0[k] + d[i]);
-    xabs = fmaxf(xabs, fabsf(x));
-    const float q1 = ni * x;                   // f x^2
-    M2 += q1;
-    const float q2 = q1 * x;                   // f x^3
-    M3 += q2;
-    M4 = fmaf(q2, x, M4);                      // f x^4
+  float M2, M3, M4, xabs;
+  {   // rest population
+    float pm1 = pxy[1][1].x;
+    if (L::D == 3) pm1 = fmaf(pm1, dz[2], pm1 + dz[2]);
+    float deq = fmaf(wr[0], pm1, wd[0]);
+    if (!SHIFTED) deq += corr[0];
+    const float ni = deq - d0;
+    r.n0 = ni;
+    const float x = ni * rcp_approx(w0[0] + d0);
+    xabs = fabsf(x);
+    M2 = ni * x;                               // f x^2
+    M3 = M2 * x;                               // f x^3
+    M4 = M3 * x;                               // f x^4
   }
+  float2 m2 = f2(0.0f), m3 = f2(0.0f), m4 = f2(0.0f);
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    const int i = 2 * k + 1;
+    const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+    float2 pm1 = pxy[cidx(cx)][cidx(cy)];
+    if (L::D == 3) {
+      const float2 a2 = fac(2, cz);
+      pm1 = fma2(pm1, a2, add2(pm1, a2));
+    }
+    const int kc = wclass<L>(i);
+    float2 deq = fma2(f2(wr[kc]), pm1, f2(wd[kc]));  // W (drho + rho (P - 1))
+    if (!SHIFTED) deq = add2(deq, make_float2(corr[i], corr[i + 1]));
+    const float2 ni = sub2(deq, dd[k]);
+    r.n2[k] = ni;
+    const float2 x = mul2(ni, rcp_approx2(add2(f2(w0[kc]), dd[k])));
+    xabs = fmaxf(xabs, fmaxf(fabsf(x.x), fabsf(x.y)));
+    const float2 q1 = mul2(ni, x);
+    const float2 q2 = mul2(q1, x);
+    if (k == 0) {
+      m2 = q1;
+      m3 = q2;
+      m4 = mul2(q2, x);
+    } else {
+      m2 = add2(m2, q1);
+      m3 = add2(m3, q2);
+      m4 = fma2(q2, x, m4);
+    }
+  }
+  M2 += m2.x + m2.y;
+  M3 += m3.x + m3.y;
+  M4 += m4.x + m4.y;
   if (!(xabs <= 0.125f)) {   // far from equilibrium, invalid, or NaN
     r.flags = NF_FAR;
     return;
@@ -211,19 +279,37 @@ __device__ __forceinline__ void node32_formula(const float (&d)[L::Q],
   const bool k8 = xabs > 0.01f;
   float M5 = 0.f, M6 = 0.f, M7 = 0.f, M8 = 0.f;
   if (k8) {
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const float x = r.n[i] * rcp_approx(w0[wclass<L>(i)] + d[i]);
+    {
+      const float x = r.n0 * rcp_approx(w0[0] + d0);
       const float x2 = x * x;
-      float p = r.n[i] * x2 * x2;   // n x^4 = f x^5
-      M5 += p;
+      float p = r.n0 * x2 * x2;   // n x^4 = f x^5
+      M5 = p;
       p *= x;
-      M6 += p;
+      M6 = p;
       p *= x;
-      M7 += p;
+      M7 = p;
       p *= x;
-      M8 += p;
+      M8 = p;
     }
+    float2 m5 = f2(0.0f), m6 = f2(0.0f), m7 = f2(0.0f), m8 = f2(0.0f);
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      const int kc = wclass<L>(2 * k + 1);
+      const float2 x = mul2(r.n2[k], rcp_approx2(add2(f2(w0[kc]), dd[k])));
+      const float2 x2 = mul2(x, x);
+      float2 p = mul2(mul2(r.n2[k], x2), x2);
+      m5 = add2(m5, p);
+      p = mul2(p, x);
+      m6 = add2(m6, p);
+      p = mul2(p, x);
+      m7 = add2(m7, p);
+      p = mul2(p, x);
+      m8 = add2(m8, p);
+    }
+    M5 += m5.x + m5.y;
+    M6 += m6.x + m6.y;
+    M7 += m7.x + m7.y;
+    M8 += m8.x + m8.y;
   }
 
   // ---- error bounds -------------------------------------------------------
@@ -308,28 +394,33 @@ __device__ __forceinline__ void node32_formula(const float (&d)[L::Q],
 // Conservation projection of n (applied to the relaxation only): removes
 // the mass/momentum that rounding left in n,
 //   n_i <- n_i - W_i (r0 + 3 c_i . r),  r0 = sum n_i,  r = sum c_i n_i,
-// using sum W = 1 and sum W c c = I / 3.  Returns t_i for every i through
-// `emit(i, W_i t_i)`.
-template <class L, class Emit>
-__device__ __forceinline__ void projection(const float (&n)[L::Q], Emit emit) {
+// using sum W = 1 and sum W c c = I / 3.  Emits W_i t_i through
+// emit0(W_0 t_0) for the rest population and emit2(k, (W t) of pair k).
+template <class L, class Emit0, class Emit2>
+__device__ __forceinline__ void projection(const N32<L>& r, Emit0 emit0,
+                                           Emit2 emit2) {
   float r0, rx, ry, rz;
-  moment_sums<L>([&](int i) { return n[i]; }, r0, rx, ry, rz);
-  float tx[3], txy[3][3];
-  tx[1] = r0;
-  tx[2] = fmaf(3.0f, rx, r0);
-  tx[0] = fmaf(-3.0f, rx, r0);
+  moments2<L>(r.n0, r.n2, r0, rx, ry, rz);
+  // t for lane-x velocity c in lane x and for -c in lane y
+  const float2 R0 = f2(r0), RX = f2(rx), RY = f2(ry), RZ = f2(rz);
+  float2 tx[3], txy[3][3];
+  tx[1] = R0;
+  tx[2] = fma2(lane_sign(3), RX, R0);
+  tx[0] = fma2(lane_sign(-3), RX, R0);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     txy[a][1] = tx[a];
-    txy[a][2] = fmaf(3.0f, ry, tx[a]);
-    txy[a][0] = fmaf(-3.0f, ry, tx[a]);
+    txy[a][2] = fma2(lane_sign(3), RY, tx[a]);
+    txy[a][0] = fma2(lane_sign(-3), RY, tx[a]);
   }
+  emit0(L::wf(0) * r0);
 #pragma unroll
-  for (int i = 0; i < L::Q; ++i) {
-    const int cx = cidx(L::c(i, 0)), cy = cidx(L::c(i, 1)), cz = L::c(i, 2);
-    float t = txy[cx][cy];
-    if (cz != 0) t = fmaf(3.0f * (float)cz, rz, t);
-    emit(i, L::wf(i) * t);
+  for (int k = 0; k < npairs<L>(); ++k) {
+    const int i = 2 * k + 1;
+    const int cz = L::c(i, 2);
+    float2 t = txy[cidx(L::c(i, 0))][cidx(L::c(i, 1))];
+    if (cz != 0) t = fma2(lane_sign(3 * cz), RZ, t);
+    emit2(k, mul2(f2(L::wf(i)), t));
   }
 }
 

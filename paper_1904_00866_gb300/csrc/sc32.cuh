@@ -135,29 +135,43 @@ __device__ __forceinline__ bool sc32_node_in(In in, float rho0f, double rho0,
                                              float* amap, Acc32& acc,
                                              Out out) {
   constexpr int Q = L::Q;
-  float d[Q];
+  constexpr int P = npairs<L>();
+  float d0;
+  float2 dd[P];
+  {
+    const float v = in(0);
+    d0 = SHIFTED ? v : v - L::wf(0) * rho0f;
+  }
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const float v = in(i);
-    d[i] = SHIFTED ? v : v - L::wf(i) * rho0f;
+  for (int k = 0; k < P; ++k) {
+    const float2 v = make_float2(in(2 * k + 1), in(2 * k + 2));
+    dd[k] = SHIFTED ? v : sub2(v, f2(L::wf(2 * k + 1) * rho0f));
   }
   float a_extra = 0.0f;
   if (!SHIFTED) {
     // delta_i = v_i - s_i is exact unless v_i leaves [s_i/2, 2 s_i]
-    float A = 0.0f;
+    float A = fabsf(d0);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) A += fabsf(d[i]);
+    for (int k = 0; k < P; ++k) A += fabsf(dd[k].x) + fabsf(dd[k].y);
     a_extra = 2.0f * 5.9604645e-8f * A / rho0f;
   }
   N32<L> r;
-  node32_formula<L, SHIFTED>(d, rho0f, corr_rho, corr, a_extra, r);
+  node32_formula<L, SHIFTED>(d0, dd, rho0f, corr_rho, corr, a_extra, r);
   if (r.flags & NF_FAR) return false;
   // relax with the conservation-projected n:  f~ = f + alpha beta n
   const float ab = r.alpha * beta;
-  projection<L>(r.n, [&](int i, float wt) {
-    const float nv = fmaf(ab, r.n[i] - wt, d[i]);
-    out(i, SHIFTED ? nv : nv + L::wf(i) * rho0f);
-  });
+  projection<L>(
+      r,
+      [&](float wt) {
+        const float nv = fmaf(ab, r.n0 - wt, d0);
+        out(0, SHIFTED ? nv : nv + L::wf(0) * rho0f);
+      },
+      [&](int k, float2 wt) {
+        float2 nv = fma2(f2(ab), sub2(r.n2[k], wt), dd[k]);
+        if (!SHIFTED) nv = add2(nv, f2(L::wf(2 * k + 1) * rho0f));
+        out(2 * k + 1, nv.x);
+        out(2 * k + 2, nv.y);
+      });
   if (amap) *amap = r.alpha;
   if (DIAG) {
     acc.nodes += 1;
