@@ -11,8 +11,9 @@
 // The autotuner times dry steps (read buf[p], write buf[p^1] without
 // advancing p, so the state is untouched) for each candidate block size and
 // blocks-per-SM, and keeps the fastest per membership signature (lattice
-// types and power-of-two size classes) in a process-wide cache, optionally
-// persisted as JSON in the file named by ELBM_AUTOTUNE_CACHE.
+// types present and the power-of-two class of the total node count) in a
+// process-wide cache, optionally persisted as JSON in the file named by
+// ELBM_AUTOTUNE_CACHE.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -236,12 +237,15 @@ static elbm_status ensure_tables(elbm_batch* b) {
   return ELBM_OK;
 }
 
+static void drop_graph(elbm_batch* b);
+
 static elbm_status ensure_queue(elbm_batch* b) {
   size_t need = 0;
   for (auto& mm : b->m)
     if (mm.live) need += mm.n;
   if (need <= b->queue_cap) return ELBM_OK;
   cudaStreamSynchronize(b->stream);
+  drop_graph(b);   // the captured launches hold the old queue pointer
   const size_t old_cap = b->queue_cap;
   bfree(b, b->d_queue, old_cap * sizeof(unsigned long long));
   b->d_queue = nullptr;
@@ -363,18 +367,23 @@ static void drop_graph(elbm_batch* b) {
 }
 
 static elbm_status autotune(elbm_batch* b) {
+  // Signature of the membership: which lattice types are present and the
+  // power-of-two class of the total node count.  The best launch shape
+  // depends on these (per-node cost, tail of the tile list), not on the
+  // individual members, so members joining or leaving rarely re-tune.
   std::string key;
   {
-    std::vector<std::string> parts;
+    bool q9 = false, q27 = false;
+    unsigned long long total = 0;
     for (auto& mm : b->m) {
       if (!mm.live) continue;
-      int cls = 0;
-      while ((1u << cls) < mm.n) ++cls;
-      parts.push_back(std::string(mm.lattice == ELBM_D3Q27 ? "Q27:" : "Q9:") +
-                      std::to_string(cls));
+      (mm.lattice == ELBM_D3Q27 ? q27 : q9) = true;
+      total += mm.n;
     }
-    std::sort(parts.begin(), parts.end());
-    for (auto& s : parts) key += s + ",";
+    int cls = 0;
+    while ((1ull << cls) < total) ++cls;
+    key = std::string(q9 ? "Q9" : "") + (q27 ? "Q27" : "") + ":" +
+          std::to_string(cls);
   }
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -642,9 +651,9 @@ elbm_status elbm_batch_step(elbm_batch* b, long long nsteps) {
   if (nsteps < 0) return bfail(b, ELBM_EINVAL, "nsteps must be >= 0");
   if (!b->d_desc) return bfail(b, ELBM_ESTATE, "batch has no members");
   if (b->autotune && !b->tuned) {
+    // a changed launch shape makes the graph check below re-capture
     elbm_status st = autotune(b);
     if (st) return st;
-    drop_graph(b);
   }
   const int grid = sm_count() * b->bps;
   long long left = nsteps;

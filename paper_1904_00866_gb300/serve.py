@@ -76,6 +76,8 @@ class Server:
         self.bursts = 0
         self.peak_used = 0.0
         self.peak_active = 0
+        # host seconds spent admitting, waiting for bursts and retiring
+        self.t_admit = self.t_burst = self.t_retire = 0.0
 
     # -- submission ----------------------------------------------------------
     def submit(self, req):
@@ -134,8 +136,10 @@ class Server:
         t0 = self.clock() if t0 is None else t0
         self._t0 = t0
         while self.waiting or self.active:
-            now = self.clock() - t0
-            self._admit(now)
+            ta = self.clock()
+            self._admit(ta - t0)
+            tb = self.clock()
+            self.t_admit += tb - ta
             if not self.active:
                 if self.waiting:
                     wait = self.waiting[0][0] - (self.clock() - t0)
@@ -144,8 +148,11 @@ class Server:
                 continue
             self.batch.step(self.burst)
             self.batch.sync()
+            tc = self.clock()
+            self.t_burst += tc - tb
             self.bursts += 1
             self._retire()
+            self.t_retire += self.clock() - tc
         return self.report()
 
     def report(self):
@@ -165,6 +172,9 @@ class Server:
             "bursts": self.bursts,
             "peak_resident": self.peak_active,
             "peak_budget_bytes": self.peak_used,
+            "host_s": {"admit": round(self.t_admit, 3),
+                       "bursts": round(self.t_burst, 3),
+                       "retire": round(self.t_retire, 3)},
         }
 
 
