@@ -5,6 +5,7 @@
 #include "sc16.cuh"
 #include "sc32.cuh"
 #include "sc32_tma.cuh"
+#include "sc32w.cuh"
 
 #include <stdlib.h>
 #include <string.h>
@@ -126,18 +127,54 @@ static cudaError_t launch_tma_one(const StepParams& p, int grid,
   return cudaGetLastError();
 }
 
-// ELBM_SC32_VARIANT=tma selects the bulk-copy row-staging kernel for
-// lattices with nx % 256 == 0.  It reads exactly the algorithmic bytes but
-// runs slower on GB300 than the per-thread cp.async gather (about 16 vs 22
-// GLUPS for D3Q27 at 512^3: its single-row copies serialise on the mbarrier
-// wait), so the gather kernel is the default.
-static bool tma_allowed() {
+// Wide-gather kernel for FP32-shifted lattices with nx % 64 == 0.
+template <class L, int DIAG, int CHECK>
+static cudaError_t launch_wide_one(const StepParams& p, int grid,
+                                   cudaStream_t s, int* grid_used) {
+  auto k = k_sc32w<L, DIAG, CHECK>;
+  const int smem =
+      kWideWarps * 2 * wide_stage_floats<L>() * (int)sizeof(float);
+  static bool configured = false;   // per instantiation
+  if (!configured) {
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    configured = true;
+  }
+  if (grid <= 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kWideThreads,
+                                                  smem);
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 8) per_sm = 8;   // partials rows bound
+    long long g = (long long)sms * per_sm;
+    const long long blocks = (p.n / kWideSeg + kWideWarps - 1) / kWideWarps;
+    if (blocks < g) g = blocks;
+    grid = g < 1 ? 1 : (int)g;
+  }
+  if (grid_used) *grid_used = grid;
+  k<<<grid, kWideThreads, smem, s>>>(p);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// Kernel variant for FP32-shifted lattices, chosen once per process by
+// ELBM_SC32_VARIANT: "cpasync" (default; per-element gathers, any size),
+// "wide" (16-byte row-segment gathers, nx % 64 == 0) or "tma" (bulk-copy
+// row staging, nx % 256 == 0).  Both alternatives read exactly the
+// algorithmic bytes but fit fewer warps per SM; on the D3Q27 512^3 workload
+// "wide" ties with the default and "tma" runs about a quarter slower.
+// Sizes a variant does not cover use the per-element kernel.
+enum Sc32Variant { kVarCpAsync = 0, kVarWide = 1, kVarTma = 2 };
+static int sc32_variant() {
   static int v = -1;
   if (v < 0) {
     const char* e = getenv("ELBM_SC32_VARIANT");
-    v = (e && strcmp(e, "tma") == 0) ? 1 : 0;
+    v = kVarCpAsync;
+    if (e && strcmp(e, "wide") == 0) v = kVarWide;
+    if (e && strcmp(e, "tma") == 0) v = kVarTma;
   }
-  return v == 1;
+  return v;
 }
 
 template <class L>
@@ -145,10 +182,16 @@ static cudaError_t launch_sc32(int diag, int check, const StepParams& p,
                                int grid, cudaStream_t s, int* grid_used) {
   if (p.unshifted)
     return launch_sc32_s<L, false>(diag, check, p, grid, s, grid_used);
-  if (p.nx % 256 == 0 && tma_allowed()) {
+  const int var = sc32_variant();
+  if (var == kVarTma && p.nx % 256 == 0) {
     if (check) return launch_tma_one<L, 1, 1>(p, grid, s, grid_used);
     if (diag) return launch_tma_one<L, 1, 0>(p, grid, s, grid_used);
     return launch_tma_one<L, 0, 0>(p, grid, s, grid_used);
+  }
+  if (var == kVarWide && p.nx % kWideSeg == 0) {
+    if (check) return launch_wide_one<L, 1, 1>(p, grid, s, grid_used);
+    if (diag) return launch_wide_one<L, 1, 0>(p, grid, s, grid_used);
+    return launch_wide_one<L, 0, 0>(p, grid, s, grid_used);
   }
   return launch_sc32_s<L, true>(diag, check, p, grid, s, grid_used);
 }
