@@ -49,7 +49,7 @@ FALLBACK_HBM_GBS = 6800.0
 # dram__bytes_read.sum + dram__bytes_write.sum per launch / nodes), valid
 # while the kernel sources hash to `sha`; scaled to the workload by node
 # count (traffic grows in proportion).
-TRAFFIC_RECORD = {"sha": "3a2d6ed6cd2c76e8", "bytes_per_node": 220.3766,
+TRAFFIC_RECORD = {"sha": "595261297a8770a7", "bytes_per_node": 220.7561,
                   "files": ['fp16_storage.cuh', 'lattice.cuh', 'node_fp32.cuh',
                             'node_fp64.cuh', 'sc32.cuh', 'stats.cuh',
                             'stream_collide.cuh']}

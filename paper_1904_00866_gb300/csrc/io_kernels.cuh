@@ -51,6 +51,38 @@ struct Geo {
   int shifted;   // FP32_SHIFTED storage (FP16 storage is always shifted)
 };
 
+// The same in FP32 for FP32 storage (the stored value is rounded to FP32
+// anyway): deviation W_i (drho + rho (P_i - 1)) formed
+// without cancellation, a few FP32 ulp of the deviation; FP32 runs at 64x
+// the FP64 rate on this GPU, which makes initialisation memory-bound.
+// f_out (unshifted storage) = W_i rho (1 + (P_i - 1)).
+template <class L>
+__device__ __forceinline__ void equilibrium_dev32(float rho, float drho,
+                                                  const float* u,
+                                                  float* dev_out,
+                                                  float* f_out) {
+  float dp[3], dm[3], d0[3];
+#pragma unroll
+  for (int a = 0; a < L::D; ++a) {
+    const float s = 3.0f * u[a] * u[a] / (1.0f + sqrtf(fmaf(3.0f * u[a], u[a], 1.0f)));
+    dp[a] = fmaf(3.0f, u[a], 2.0f * s);
+    dm[a] = fmaf(-3.0f, u[a], 2.0f * s);
+    d0[a] = -s;
+  }
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    float pm1 = 0.0f;   // prod (1 + d) - 1
+#pragma unroll
+    for (int a = 0; a < L::D; ++a) {
+      const int c = L::c(i, a);
+      const float d = c == 1 ? dp[a] : (c == -1 ? dm[a] : d0[a]);
+      pm1 = fmaf(pm1, d, pm1 + d);
+    }
+    dev_out[i] = L::wf(i) * fmaf(rho, pm1, drho);
+    f_out[i] = L::wf(i) * fmaf(rho, pm1, rho);
+  }
+}
+
 // Storage value of population i, f, whose deviation from W_i rho0 is dev.
 template <class L, class T>
 __device__ __forceinline__ T to_storage(const Geo& g, int i, double f,
@@ -74,24 +106,41 @@ __device__ __forceinline__ double from_storage(const Geo& g, int i, T v) {
     return h16_to_f<L>(v, i, g.rho0);
 }
 
+// (x, y, z) of a flat node index, in 32-bit arithmetic (every lattice has
+// fewer than 2^32 nodes), computed once per node.
+struct Coord {
+  int x, y, z;
+};
+__device__ __forceinline__ Coord node_coord(const Geo& g, long long node) {
+  const unsigned nd = (unsigned)node;
+  const unsigned row = nd / (unsigned)g.nx;
+  const unsigned zq = row / (unsigned)g.ny;
+  Coord c;
+  c.x = (int)(nd - row * (unsigned)g.nx);
+  c.y = (int)(row - zq * (unsigned)g.ny);
+  c.z = (int)zq;
+  return c;
+}
+
+// Flat index of node + sign * c_i (periodic).
 template <class L>
-__device__ __forceinline__ long long shifted_node(const Geo& g, long long node,
+__device__ __forceinline__ long long shifted_node(const Geo& g, const Coord& c,
                                                   int i, int sign) {
-  // node + sign * c_i (periodic)
-  int x = (int)(node % g.nx);
-  int y = (int)((node / g.nx) % g.ny);
-  int z = (int)(node / ((long long)g.nx * g.ny));
-  x += sign * L::c(i, 0);
-  y += sign * L::c(i, 1);
-  z += sign * L::c(i, 2);
+  int x = c.x + sign * L::c(i, 0);
+  int y = c.y + sign * L::c(i, 1);
+  int z = c.z + sign * L::c(i, 2);
   x = x < 0 ? x + g.nx : (x >= g.nx ? x - g.nx : x);
   y = y < 0 ? y + g.ny : (y >= g.ny ? y - g.ny : y);
   z = z < 0 ? z + g.nz : (z >= g.nz ? z - g.nz : z);
-  return ((long long)z * g.ny + y) * g.nx + x;
+  return (long long)(((unsigned)z * (unsigned)g.ny + (unsigned)y) *
+                         (unsigned)g.nx +
+                     (unsigned)x);
 }
 
 // f^0 = f^eq(rho, u); stored at x - c_i so that the pull gather of step 0
-// returns it at x.
+// returns it at x.  FP32 storage: the FP32 deviation form above; FP64 and
+// FP16 storage: the FP64 equilibrium (binary16 values are then rounded once
+// from FP64).
 template <class L, class T>
 __global__ void k_init_feq(Geo g, const double* __restrict__ rho,
                            const double* __restrict__ u, void* fv,
@@ -108,12 +157,26 @@ __global__ void k_init_feq(Geo g, const double* __restrict__ rho,
       bad |= !(fabs(uu[a]) < 1.0);
     }
     if (bad) atomicOr(err, NF_BAD_NONFINITE);
-    double dev[L::Q], fe[L::Q];
-    equilibrium_dev<L>(bad ? 1.0 : r, uu, g.rho0, dev, fe);
+    const Coord c = node_coord(g, node);
+    if constexpr (sizeof(T) != 4) {
+      double dev[L::Q], fe[L::Q];
+      equilibrium_dev<L>(bad ? 1.0 : r, uu, g.rho0, dev, fe);
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i)
-      f[i * g.ps + shifted_node<L>(g, node, i, -1)] =
-          to_storage<L, T>(g, i, fe[i], dev[i]);
+      for (int i = 0; i < L::Q; ++i)
+        f[i * g.ps + shifted_node<L>(g, c, i, -1)] =
+            to_storage<L, T>(g, i, fe[i], dev[i]);
+    } else {
+      const double rr = bad ? 1.0 : r;
+      float u32[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) u32[a] = bad ? 0.0f : (float)uu[a];
+      float dev[L::Q], fe[L::Q];
+      equilibrium_dev32<L>((float)rr, (float)(rr - g.rho0), u32, dev, fe);
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i)
+        f[i * g.ps + shifted_node<L>(g, c, i, -1)] =
+            g.shifted ? dev[i] : fe[i];
+    }
   }
 }
 
@@ -123,11 +186,12 @@ __global__ void k_set_pop(Geo g, const double* __restrict__ fin, void* fv) {
   T* __restrict__ f = static_cast<T*>(fv);
   for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
        node < g.n; node += (long long)gridDim.x * blockDim.x) {
+    const Coord c = node_coord(g, node);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
       const double v = fin[i * g.n + node];
       const double s = L::w(i) * g.rho0;
-      f[i * g.ps + shifted_node<L>(g, node, i, -1)] =
+      f[i * g.ps + shifted_node<L>(g, c, i, -1)] =
           to_storage<L, T>(g, i, v, v - s);
     }
   }
@@ -135,8 +199,8 @@ __global__ void k_set_pop(Geo g, const double* __restrict__ fin, void* fv) {
 
 template <class L, class T>
 __device__ __forceinline__ double load_pre(const Geo& g, const T* f,
-                                           long long node, int i) {
-  return from_storage<L, T>(g, i, f[i * g.ps + shifted_node<L>(g, node, i, -1)]);
+                                           const Coord& c, int i) {
+  return from_storage<L, T>(g, i, f[i * g.ps + shifted_node<L>(g, c, i, -1)]);
 }
 
 // Storage -> pre-collision populations / moments (gather).
@@ -145,8 +209,9 @@ __global__ void k_get_pop(Geo g, const void* fv, double* __restrict__ out) {
   const T* __restrict__ f = static_cast<const T*>(fv);
   for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
        node < g.n; node += (long long)gridDim.x * blockDim.x) {
+    const Coord c = node_coord(g, node);
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) out[i * g.n + node] = load_pre<L, T>(g, f, node, i);
+    for (int i = 0; i < L::Q; ++i) out[i * g.n + node] = load_pre<L, T>(g, f, c, i);
   }
 }
 
@@ -157,10 +222,10 @@ __global__ void k_get_nodes(Geo g, const void* fv,
   const T* __restrict__ f = static_cast<const T*>(fv);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count;
        k += gridDim.x * blockDim.x) {
-    const long long node = nodes[k];
+    const Coord c = node_coord(g, nodes[k]);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i)
-      out[(long long)k * L::Q + i] = load_pre<L, T>(g, f, node, i);
+      out[(long long)k * L::Q + i] = load_pre<L, T>(g, f, c, i);
   }
 }
 
@@ -171,14 +236,38 @@ __global__ void k_moments(Geo g, const void* fv, double* __restrict__ rho_out,
   for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
        node < g.n; node += (long long)gridDim.x * blockDim.x) {
     double rho = 0.0, j[3] = {0.0, 0.0, 0.0};
+    const Coord c = node_coord(g, node);
+    if (sizeof(T) == 4 && g.shifted) {
+      // FP32 deviations: rho = rho0 + sum delta, j = sum c delta (the
+      // W_i rho0 terms carry no momentum), with each delta split into a
+      // 2^-20-grid part (summed exactly in FP32) and a remainder below
+      // 2^-21 (summed in FP32: error ~1e-11), combined in FP64
+      float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-      const double v = load_pre<L, T>(g, f, node, i);
-      rho += v;
+      for (int i = 0; i < L::Q; ++i) {
+        const float v = (float)f[i * g.ps + shifted_node<L>(g, c, i, -1)];
+        const float hi = (v + 12.0f) - 12.0f, lo = v - hi;
+        h[0] += hi;
+        l[0] += lo;
 #pragma unroll
-      for (int a = 0; a < L::D; ++a) {
-        if (L::c(i, a) == 1) j[a] += v;
-        if (L::c(i, a) == -1) j[a] -= v;
+        for (int a = 0; a < L::D; ++a) {
+          if (L::c(i, a) == 1) { h[a + 1] += hi; l[a + 1] += lo; }
+          if (L::c(i, a) == -1) { h[a + 1] -= hi; l[a + 1] -= lo; }
+        }
+      }
+      rho = g.rho0 + ((double)h[0] + (double)l[0]);
+#pragma unroll
+      for (int a = 0; a < L::D; ++a) j[a] = (double)h[a + 1] + (double)l[a + 1];
+    } else {
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        const double v = load_pre<L, T>(g, f, c, i);
+        rho += v;
+#pragma unroll
+        for (int a = 0; a < L::D; ++a) {
+          if (L::c(i, a) == 1) j[a] += v;
+          if (L::c(i, a) == -1) j[a] -= v;
+        }
       }
     }
     if (rho_out) rho_out[node] = rho;
@@ -198,9 +287,8 @@ __global__ void k_vorticity2(Geo g, const double* __restrict__ u,
   double acc = 0.0;
   for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
        node < g.n; node += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(node % g.nx);
-    const int y = (int)((node / g.nx) % g.ny);
-    const int z = (int)(node / ((long long)g.nx * g.ny));
+    const Coord c = node_coord(g, node);
+    const int x = c.x, y = c.y, z = c.z;
     auto at = [&](int a, int xx, int yy, int zz) {
       xx = xx < 0 ? xx + g.nx : (xx >= g.nx ? xx - g.nx : xx);
       yy = yy < 0 ? yy + g.ny : (yy >= g.ny ? yy - g.ny : yy);

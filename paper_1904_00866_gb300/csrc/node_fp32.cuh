@@ -31,6 +31,8 @@
 //                              below the root of Eq. (4));
 //   else (node within FP32 noise of equilibrium) -> alpha = 1, for which
 //                              H(f*) = H(f^eq) <= H(f) holds exactly.
+// A node whose n evaluates to exactly zero in FP32 (the degenerate case of
+// the paper seen at FP32 resolution) also takes alpha = 1.
 // When |Delta H(2)| <= e2 the decision is flagged NF_BAND.
 //
 // Opposite-velocity populations are processed in pairs with packed f32x2
@@ -271,8 +273,13 @@ __device__ __forceinline__ void node32_formula(
     r.flags = NF_FAR;
     return;
   }
-  if (xabs == 0.0f) {        // f^eq == f in FP32
+  if (xabs == 0.0f) {
+    // f^eq == f in FP32 only: the exact state may still differ from its
+    // equilibrium below FP32 resolution, where alpha = 2 can raise H by a
+    // rounding-level amount.  alpha = 1 (f* = f^eq) keeps H(f*) <= H(f)
+    // exactly; the relaxation writes f unchanged either way (n = 0).
     r.flags = NF_DEGENERATE;
+    r.alpha = 1.0f;
     return;
   }
   // longer series for nodes further from equilibrium
