@@ -1,0 +1,108 @@
+"""Turbulent and transitional runs: FP32-shifted storage against the FP64
+path (itself pinned to the oracle at 1e-12 per population) through kinetic
+energy and enstrophy histories, within 1 % at every sample -- the tolerance
+the method's precision target sets for turbulent cases.
+
+  * the double shear layer of the shear-layer experiment scaled to 1024^2
+    (U = 0.04, lambda = 80, perturbation 2e-3, Re = U M / nu = 30000),
+    20000 steps sampled every 1000, with the per-node alpha map recorded at
+    every sample (Fig. 4 style);
+  * the D3Q27 Taylor-Green vortex at Re = 1600 (u0 = 0.05, nu = u0 L / Re,
+    L = N / 2 pi) over 20 convective times t_c = L / u0, at 128^3 so that
+    the FP64 run stays near a minute.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import elbm_workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def elbm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1904_00866_gb300 as e
+    if not os.path.exists(e.LIB_PATH):
+        import __graft_entry__ as g
+        g.build()
+    e.lib()
+    return e
+
+
+def _energy(rho, u):
+    return 0.5 * float(np.sum(rho * np.sum(u * u, axis=0)))
+
+
+def _history(g, samples, every):
+    """Energy and enstrophy after each of `samples` runs of `every` steps."""
+    e, z = [], []
+    for _ in range(samples):
+        g.step(every, "formula")
+        e.append(_energy(*g.moments()))
+        z.append(g.enstrophy())
+    return np.array(e), np.array(z)
+
+
+def test_shear_layer_1024_fp32_vs_fp64_histories(elbm):
+    n, U = 1024, 0.04
+    nu = U * n / 30000.0
+    rho, u = W.shear_layer(n, U=U)
+    runs = {}
+    for dtype in ["fp64", "fp32_shifted"]:
+        g = elbm.Lattice("D2Q9", n, n, 1, nu=nu, dtype=dtype)
+        g.set_diagnostics(diag_every=1000, alpha_map_every=1000)
+        g.init_fields(rho, u)
+        e, z, amin, low = [], [], [], []
+        for _ in range(20):
+            g.step(1000, "formula")
+            e.append(_energy(*g.moments()))
+            z.append(g.enstrophy())
+            a = g.alpha_map()
+            assert np.all((a >= 1.0) & (a <= 2.0))
+            amin.append(float(a.min()))
+            low.append(float(np.mean(a < 2.0)))
+            assert g.entropy_stats()["n_violations"] == 0
+        runs[dtype] = (np.array(e), np.array(z), amin, low)
+    e64, z64, amin64, low64 = runs["fp64"]
+    e32, z32, amin, low = runs["fp32_shifted"]
+    de = np.abs(e32 / e64 - 1).max()
+    dz = np.abs(z32 / z64 - 1).max()
+    print("shear layer 1024^2, 20000 steps: max rel dev energy %.2e, "
+          "enstrophy %.2e" % (de, dz))
+    # alpha below 2 marks either Eq. (9) or, in FP32, a node whose
+    # non-equilibrium part is below FP32 resolution (alpha = 1, H-safe)
+    print("  alpha min FP64 %.4f / FP32 %.4f; share alpha < 2 per sample "
+          "FP64 %s / FP32 %s" % (min(amin64), min(amin),
+                                 np.round(low64, 3).tolist(),
+                                 np.round(low, 3).tolist()))
+    assert de < 1e-2 and dz < 1e-2
+
+
+def test_taylor_green_re1600_fp32_vs_fp64_histories(elbm):
+    n, u0 = 128, 0.05
+    L = n / (2 * math.pi)
+    nu = u0 * L / 1600.0
+    tc = int(round(L / u0))
+    rho, u = W.taylor_green_3d(n, u0)
+    hist = {}
+    for dtype in ["fp64", "fp32_shifted"]:
+        g = elbm.Lattice("D3Q27", n, n, n, nu=nu, dtype=dtype)
+        g.set_diagnostics(diag_every=tc)
+        g.init_fields(rho, u)
+        hist[dtype] = _history(g, 20, tc)
+        assert g.entropy_stats()["n_violations"] == 0
+        g.close()
+    e64, z64 = hist["fp64"]
+    e32, z32 = hist["fp32_shifted"]
+    de = np.abs(e32 / e64 - 1)
+    dz = np.abs(z32 / z64 - 1)
+    print("TGV Re=1600 128^3, 20 t_c: max rel dev energy %.2e, enstrophy "
+          "%.2e; enstrophy peak at %d t_c" % (de.max(), dz.max(),
+                                               int(np.argmax(z64)) + 1))
+    assert de.max() < 1e-2 and dz.max() < 1e-2
