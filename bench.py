@@ -493,18 +493,21 @@ def e2e(elbm, args, n, nu, stream, world):
     g.step(args.warmup, "formula")
     g.sync()
     barrier(world)
+    import ctypes
     t0 = time.perf_counter()
     g.init_fields(rho_h.numpy(), u_h.numpy())
+    t1 = time.perf_counter()
     for _ in range(args.steps):
         g.step(1, "formula")
         g.entropy_stats()
-    import ctypes
+    t2 = time.perf_counter()
     st = elbm.lib().elbm_moments(
         g._h, ctypes.cast(out_rho.data_ptr(), elbm._DP),
         ctypes.cast(out_u.data_ptr(), elbm._DP))
     if st:
         raise RuntimeError("moments failed")
-    dt = time.perf_counter() - t0
+    t3 = time.perf_counter()
+    dt = t3 - t0
     dt = max_over_ranks(dt, world)
     g.close()
     nodes = n ** 3
@@ -515,7 +518,10 @@ def e2e(elbm, args, n, nu, stream, world):
             // args.steps,
             "d2h_bytes_per_step": int((out_rho.numel() + out_u.numel()) * 8)
             // args.steps + stats_bytes,
-            "seconds": round(dt, 3)}
+            "seconds": round(dt, 3),
+            "phases_ms": {"init": round((t1 - t0) * 1e3, 1),
+                          "steps": round((t2 - t1) * 1e3, 1),
+                          "readback": round((t3 - t2) * 1e3, 1)}}
 
 
 def run_reference(args):
