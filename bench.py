@@ -83,6 +83,9 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=100)
+    ap.add_argument("--batch-every", type=int, default=1,
+                    help="keep every k-th member of each lattice type of "
+                         "the batched mix")
     ap.add_argument("--storage", default="fp32_shifted",
                     choices=["fp32_shifted", "fp16_shifted"],
                     help="population storage of the timed lattice")
@@ -267,14 +270,18 @@ def secondary(elbm, stream):
     return out
 
 
-def batched(elbm, steps=48):
+def batched(elbm, steps=48, every=1):
     """The 64-lattice mixed batch (half D2Q9 64..1024^2, half D3Q27
     32..192^3, nu log-uniform in [1e-5, 1e-2], random-phase low-mode flow):
     one persistent launch per step, graph-replayed bursts, autotuned launch
-    shape.  MLUPS over all members, device-timed."""
+    shape.  MLUPS over all members, device-timed.  every > 1 keeps every
+    every-th member of each lattice type (a smaller batch of the same mix,
+    for profiling)."""
     import torch
     import elbm_workloads as W
     specs = W.batch_specs()
+    specs = ([sp for sp in specs if sp["lattice"] == "D2Q9"][::every] +
+             [sp for sp in specs if sp["lattice"] == "D3Q27"][::every])
     b = elbm.Batch(burst=16, use_graphs=True, autotune=True)
     nodes = 0
     for sp in specs:
@@ -460,7 +467,7 @@ def run_elbm(args):
     if not args.no_secondary and rank == 0:
         result["secondary"] = secondary(elbm, stream)
     if not args.no_batch and rank == 0:
-        result["batched"] = batched(elbm)
+        result["batched"] = batched(elbm, every=args.batch_every)
     if not args.no_serve and rank == 0:
         result["serving"] = serving(elbm, args.serve_requests)
     if not args.no_cpu and rank == 0 and world == 1:

@@ -157,6 +157,8 @@ struct elbm_batch {
   // device tables
   MemberDesc* d_desc = nullptr;
   unsigned* d_begin = nullptr;
+  unsigned char* d_tmem = nullptr;   // member index of every tile
+  size_t tmem_cap = 0;
   int* d_count = nullptr;
   MemberStats* d_stats = nullptr;
   unsigned* d_far_count = nullptr;
@@ -166,6 +168,7 @@ struct elbm_batch {
   // host mirrors
   std::vector<MemberDesc> h_desc;
   std::vector<unsigned> h_begin;
+  std::vector<unsigned char> h_tmem;
   std::vector<int> h_member_of;   // position in the tile list -> member id
   // options
   int diag_every = 0;
@@ -262,6 +265,7 @@ static BatchParams batch_params(elbm_batch* b) {
   BatchParams bp;
   bp.members = b->d_desc;
   bp.tile_begin = b->d_begin;
+  bp.tile_member = b->d_tmem;
   bp.count = b->d_count;
   bp.stats = b->d_stats;
   bp.far_queue = b->d_queue;
@@ -308,13 +312,33 @@ static int build_tables(elbm_batch* b, int burst, bool diag, int tb,
     b->h_member_of.push_back(id);
     b->h_begin.push_back(b->h_begin.back() + (mm.n + tb - 1) / tb);
   }
+  b->h_tmem.resize(b->h_begin.back());
+  for (size_t k = 0; k + 1 < b->h_begin.size(); ++k)
+    std::fill(b->h_tmem.begin() + b->h_begin[k],
+              b->h_tmem.begin() + b->h_begin[k + 1], (unsigned char)k);
   return (int)b->h_desc.size();
 }
 
 static elbm_status upload_tables(elbm_batch* b) {
   const int count = (int)b->h_desc.size();
+  const size_t tiles = b->h_tmem.size();
+  if (tiles > b->tmem_cap) {
+    // the captured launches hold the table pointer: re-capture after growth
+    cudaStreamSynchronize(b->stream);
+    drop_graph(b);
+    const size_t cap = std::max(tiles + tiles / 4 + 4096, 2 * b->tmem_cap);
+    bfree(b, b->d_tmem, b->tmem_cap);
+    b->d_tmem = nullptr;
+    b->tmem_cap = 0;
+    b->d_tmem = (unsigned char*)balloc(b, cap);
+    if (!b->d_tmem) return bfail(b, ELBM_ENOMEM, "tile table allocation failed");
+    b->tmem_cap = cap;
+  }
   cudaError_t e = cudaSuccess;
-  if (count > 0)
+  if (tiles > 0)
+    e = cudaMemcpyAsync(b->d_tmem, b->h_tmem.data(), tiles,
+                        cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess && count > 0)
     e = cudaMemcpyAsync(b->d_desc, b->h_desc.data(),
                         sizeof(MemberDesc) * count, cudaMemcpyHostToDevice,
                         b->stream);
@@ -477,6 +501,7 @@ void elbm_batch_destroy(elbm_batch* b) {
   bfree(b, b->d_queue, b->queue_cap * sizeof(unsigned long long));
   bfree(b, b->d_desc, sizeof(MemberDesc) * kBatchMaxMembers);
   bfree(b, b->d_begin, sizeof(unsigned) * (kBatchMaxMembers + 1));
+  bfree(b, b->d_tmem, b->tmem_cap);
   bfree(b, b->d_count, 256);
   bfree(b, b->d_stats, sizeof(MemberStats) * kBatchMaxMembers);
   bfree(b, b->d_far_count, 256);

@@ -3,9 +3,11 @@
 //
 // Members may differ in lattice type (D2Q9 / D3Q27), size and viscosity.
 // Each member's lattice is cut into tiles of TB consecutive nodes; the tiles
-// of all stepping members form one flat list whose prefix offsets live in
-// device memory, so a launch (or a captured CUDA graph of launches) reads
-// the current membership at run time.  Blocks walk the list with a grid
+// of all stepping members form one flat list whose prefix offsets and
+// per-tile member index live in device memory, so a launch (or a captured
+// CUDA graph of launches) reads the current membership at run time.  The
+// per-tile index replaces a per-thread binary search over the prefix (a
+// chain of dependent shared-memory loads on every node).  Blocks walk the list with a grid
 // stride and the same cp.async double-buffered gather / shared-memory
 // compute as the single-lattice kernel; a tile's block switches on its
 // member's lattice type (uniform per block).
@@ -50,6 +52,7 @@ struct MemberStats {
 struct BatchParams {
   const MemberDesc* members;
   const unsigned* tile_begin;   // [count + 1] tile prefix of the members
+  const unsigned char* tile_member;   // [tiles] member of each tile
   const int* count;             // members in the tile list
   MemberStats* stats;           // [kBatchMaxMembers]
   unsigned long long* far_queue;   // (member << 32) | node
@@ -61,19 +64,6 @@ struct BatchParams {
 
 __device__ __forceinline__ float* pick(const MemberDesc& m, int parity) {
   return (parity & 1) ? m.buf[1] : m.buf[0];
-}
-
-__device__ __forceinline__ int find_member(const unsigned* begin, int count,
-                                           unsigned tile) {
-  int lo = 0, hi = count;   // begin[lo] <= tile < begin[hi]
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (begin[mid] <= tile)
-      lo = mid;
-    else
-      hi = mid;
-  }
-  return lo;
 }
 
 template <class L, int TB>
@@ -172,8 +162,7 @@ __global__ void __launch_bounds__(TB, 2048 / TB / 4)
 
   unsigned tile = blockIdx.x;
   int stage = 0;
-  auto issue = [&](unsigned t, float* sm) {
-    const int mi = find_member(s_begin, count, t);
+  auto issue = [&](unsigned t, int mi, float* sm) {
     const MemberDesc m = bp.members[mi];   // by value: no reloads after stores
     if (bp.step >= m.steps_left) return;   // member finished in this burst
     const unsigned local = t - s_begin[mi];
@@ -182,17 +171,24 @@ __global__ void __launch_bounds__(TB, 2048 / TB / 4)
     else
       batch_issue<D2Q9, TB>(m, bp.step, sm, local);
   };
-  if (tile < total) issue(tile, smem);
+  // member indices of this tile and the next are carried in registers; the
+  // one after is loaded an iteration ahead (the table streams from L2)
+  int mi_cur = tile < total ? bp.tile_member[tile] : 0;
+  int mi_next = tile + gridDim.x < total ? bp.tile_member[tile + gridDim.x] : 0;
+  if (tile < total) issue(tile, mi_cur, smem);
   cp_async_commit();
   for (; tile < total; tile += gridDim.x) {
-    const unsigned next = tile + gridDim.x;
-    if (next < total) issue(next, smem + (stage ^ 1) * kStage);
+    const unsigned next = tile + gridDim.x, after = next + gridDim.x;
+    const int mi_after = after < total ? bp.tile_member[after] : 0;
+    if (next < total) issue(next, mi_next, smem + (stage ^ 1) * kStage);
     cp_async_commit();
     cp_async_wait<1>();
     const float* sm = smem + stage * kStage + threadIdx.x;
     stage ^= 1;
 
-    const int mi = find_member(s_begin, count, tile);
+    const int mi = mi_cur;
+    mi_cur = mi_next;
+    mi_next = mi_after;
     const MemberDesc m = bp.members[mi];   // by value: no reloads after stores
     if (bp.step >= m.steps_left) continue;   // uniform per block
     const unsigned node = (tile - s_begin[mi]) * TB + threadIdx.x;
