@@ -169,7 +169,10 @@ ELBM_API elbm_status elbm_set_diagnostics(elbm_handle *h, int diag_every,
 
 /* f^0 = f^eq(rho, u) at every node.  rho: [nz][ny][nx] > 0,
  * u: [d][nz][ny][nx] with |u_a| < 1, FP64 host buffers.  Resets the step
- * counter to 0 and sets rho0 to the FP32-rounded mean of rho. */
+ * counter to 0 and sets rho0 to the FP32-rounded mean of rho.
+ * The first call of elbm_init_fields, elbm_moments or elbm_enstrophy
+ * allocates a device staging buffer of (1 + d) x n doubles, which the
+ * handle keeps (and reuses) until elbm_destroy. */
 ELBM_API elbm_status elbm_init_fields(elbm_handle *h, const double *rho,
                              const double *u);
 /* Same with device pointers (on the handle's device, FP64). */
@@ -183,11 +186,13 @@ ELBM_API elbm_status elbm_set_populations(elbm_handle *h, const double *f);
 /* Advance nsteps >= 0 steps of Eq. (1) with the given alpha mode.
  * Asynchronous on the handle's stream.
  * FP32 FORMULA: Delta H(2) and Delta H(1) are evaluated in FP32 from the
- * moments sum_i f_i x_i^k (k = 2..6) with a bound E on their error; alpha = 2
- * is accepted only when Delta H(2) + E <= 0, otherwise alpha is the Eq. (9)
- * chord evaluated on the upper bounds and rounded down, so H(f*(alpha)) <=
- * H(f) holds for the stored state; nodes with max|x_i| > 1/8 or
- * alpha_max < 2.5 are solved in FP64. */
+ * moments sum_i f_i x_i^k (k = 2..4, or 2..8 when max|x_i| > 1/100) with a
+ * bound E on their error; alpha = 2 is accepted only when Delta H(2) + E
+ * <= 0, otherwise alpha is the Eq. (9) chord evaluated on the upper bounds
+ * and rounded down, or 1 where neither sign is resolved in FP32 (including
+ * nodes whose f^eq - f is zero in FP32), so H(f*(alpha)) <= H(f) holds for
+ * the stored state; nodes with max|x_i| > 1/8, |u_a| >= 1/2 or invalid
+ * populations are solved in FP64. */
 ELBM_API elbm_status elbm_step(elbm_handle *h, long long nsteps, elbm_alpha_mode mode);
 
 /* Block until the handle's queued work is done; reports flagged errors. */

@@ -125,6 +125,7 @@ struct elbm_handle {
   double* partials = nullptr;
   int partial_rows_max = 0;
   double* stats_dev = nullptr;
+  double* fields = nullptr;   // (1 + D) x n doubles: rho, u staging
   unsigned* err_flags = nullptr;
   unsigned* far_count = nullptr;
   unsigned* far_queue = nullptr;
@@ -234,6 +235,15 @@ static elbm_status ensure_alpha_map(elbm_handle* h) {
   h->alpha_map = (float*)dev_alloc(h, sizeof(float) * h->n);
   if (!h->alpha_map) return fail(h, ELBM_ENOMEM, "alpha map allocation failed");
   return ELBM_OK;
+}
+
+// Device staging of one density and D velocity fields (FP64), used by
+// initialisation, moments and enstrophy.  Allocated on first use and kept
+// until the handle is destroyed, so repeated calls allocate nothing.
+static double* fields_staging(elbm_handle* h) {
+  if (!h->fields)
+    h->fields = (double*)dev_alloc(h, sizeof(double) * (1 + h->d) * h->n);
+  return h->fields;
 }
 
 static Geo geo(const elbm_handle* h) {
@@ -428,8 +438,7 @@ elbm_status elbm_init_fields(elbm_handle* h, const double* rho,
   if (!h || !rho || !u) return h ? fail(h, ELBM_EINVAL, "NULL field") : ELBM_EINVAL;
   elbm_status st = ensure_buffers(h);
   if (st) return st;
-  const size_t bytes = sizeof(double) * (1 + h->d) * h->n;
-  double* tmp = (double*)dev_alloc(h, bytes);
+  double* tmp = fields_staging(h);
   if (!tmp) return fail(h, ELBM_ENOMEM, "staging allocation failed");
   cudaError_t e = cudaMemcpyAsync(tmp, rho, sizeof(double) * h->n,
                                   cudaMemcpyHostToDevice, h->stream);
@@ -438,12 +447,10 @@ elbm_status elbm_init_fields(elbm_handle* h, const double* rho,
                         cudaMemcpyHostToDevice, h->stream);
   if (e != cudaSuccess) {
     cudaStreamSynchronize(h->stream);
-    dev_free(h, tmp);
     return cuda_fail(h, e, "copy fields");
   }
   st = init_common(h, tmp, tmp + h->n);
   cudaStreamSynchronize(h->stream);
-  dev_free(h, tmp);
   return st;
 }
 
@@ -630,8 +637,7 @@ elbm_status elbm_moments(elbm_handle* h, double* rho_out, double* u_out) {
   if (!h->allocated) return fail(h, ELBM_ESTATE, "fields not initialised");
   elbm_status st = check_errors(h);
   if (st) return st;
-  const size_t bytes = sizeof(double) * (1 + h->d) * h->n;
-  double* tmp = (double*)dev_alloc(h, bytes);
+  double* tmp = fields_staging(h);
   if (!tmp) return fail(h, ELBM_ENOMEM, "staging allocation failed");
   Geo g = geo(h);
   DISPATCH_LT(h, k_moments, g, h->f[h->cur], tmp, tmp + h->n);
@@ -643,7 +649,6 @@ elbm_status elbm_moments(elbm_handle* h, double* rho_out, double* u_out) {
     e = cudaMemcpyAsync(u_out, tmp + h->n, sizeof(double) * h->d * h->n,
                         cudaMemcpyDeviceToHost, h->stream);
   cudaError_t e2 = cudaStreamSynchronize(h->stream);
-  dev_free(h, tmp);
   if (e != cudaSuccess) return cuda_fail(h, e, "copy moments");
   if (e2 != cudaSuccess) return cuda_fail(h, e2, "moments");
   return ELBM_OK;
@@ -727,8 +732,7 @@ elbm_status elbm_enstrophy(elbm_handle* h, double* out) {
   if (!h->allocated) return fail(h, ELBM_ESTATE, "fields not initialised");
   elbm_status st = check_errors(h);
   if (st) return st;
-  const size_t bytes = sizeof(double) * (1 + h->d) * h->n;
-  double* tmp = (double*)dev_alloc(h, bytes);
+  double* tmp = fields_staging(h);
   if (!tmp) return fail(h, ELBM_ENOMEM, "staging allocation failed");
   Geo g = geo(h);
   DISPATCH_LT(h, k_moments, g, h->f[h->cur], tmp, tmp + h->n);
@@ -743,7 +747,6 @@ elbm_status elbm_enstrophy(elbm_handle* h, double* out) {
                                   sizeof(double) * grid,
                                   cudaMemcpyDeviceToHost, h->stream);
   cudaError_t e2 = cudaStreamSynchronize(h->stream);
-  dev_free(h, tmp);
   if (e != cudaSuccess) return cuda_fail(h, e, "copy enstrophy");
   if (e2 != cudaSuccess) return cuda_fail(h, e2, "enstrophy");
   double s = 0.0;

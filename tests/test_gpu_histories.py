@@ -67,7 +67,13 @@ def test_shear_layer_1024_fp32_vs_fp64_histories(elbm):
             assert np.all((a >= 1.0) & (a <= 2.0))
             amin.append(float(a.min()))
             low.append(float(np.mean(a < 2.0)))
+            below = a[a < 2.0]
             assert g.entropy_stats()["n_violations"] == 0
+        # at the last sample: how far below 2 the alpha < 2 nodes sit
+        q = (np.quantile(2.0 - below, [0.5, 0.99]) if below.size
+             else np.zeros(2))
+        print("  %s: 2 - alpha over alpha < 2 nodes, median %.2e, 99th "
+              "percentile %.2e" % (dtype, q[0], q[1]))
         runs[dtype] = (np.array(e), np.array(z), amin, low)
     e64, z64, amin64, low64 = runs["fp64"]
     e32, z32, amin, low = runs["fp32_shifted"]
