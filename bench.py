@@ -176,13 +176,22 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """Largest x over the ranks (the slowest replica's time)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_mlups(nodes_per_rank, steps, world, max_ms):
+    """Lattice updates of all replicas per second (in millions), over the
+    slowest replica's time: weak scaling, every rank advances its own
+    lattice of the same size."""
+    return nodes_per_rank * steps * world / (max_ms * 1e3)
 
 
 def make_lattice(elbm, lat, n, dtype, nu, rho_dev=None, u_dev=None):
@@ -398,7 +407,7 @@ def run_elbm(args):
     barrier(world)
     ms = max_over_ranks(ms, world)
     nodes = n ** 3
-    value = nodes * args.steps * world / (ms * 1e3)
+    value = whole_job_mlups(nodes, args.steps, world, ms)
     hbm, hbm_kind = peaks()
     kernel_ms = kms / max(nk, 1)
     achieved = BYTES_PER_LU[("D3Q27", esize)] * nodes / (kernel_ms * 1e-3) / 1e9
