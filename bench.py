@@ -556,6 +556,8 @@ def run_reference(args):
     o.step(args.steps, threads=threads)
     dt = time.perf_counter() - t0
     value = n ** 3 * args.steps / dt / 1e6
+    # the same metric name as the CUDA arm's line for this storage
+    fp16 = args.storage == "fp16_shifted"
     print(json.dumps({
         "impl": "reference",
         "metric": "MLUPS (D3Q27 FORMULA %s)" % (
