@@ -91,3 +91,69 @@ def test_fig5_counter_fp32_within_band(elbm, oracle_counts):
     assert np.all(short <= band / nodes + 0.005), (short - band / nodes).max()
     print("Fig. 5 share, FP32 vs oracle: max shortfall %.4f, median share %.3f"
           % (short.max(), np.median(got[1:] / nodes)))
+
+
+def _vorticity(u):
+    """omega_z = dv/dx - du/dy (central differences, periodic), u: (2, 1, n, n)."""
+    ux, uy = u[0, 0], u[1, 0]
+    dvdx = 0.5 * (np.roll(uy, -1, axis=1) - np.roll(uy, 1, axis=1))
+    dudy = 0.5 * (np.roll(ux, -1, axis=0) - np.roll(ux, 1, axis=0))
+    return dvdx - dudy
+
+
+def _run_to_t1(elbm, mode):
+    """Vorticity at t = 1 (step T) and the alpha map of its collision."""
+    g = GOLD["double_shear_layer"]
+    n = g["M"]
+    rho, u = W.shear_layer(n, g["U"], g["lambda"], g["perturbation"])
+    lat = elbm.Lattice("D2Q9", n, n, 1, nu=g["nu"], dtype="fp64")
+    lat.set_diagnostics(diag_every=100, alpha_map_every=g["T"])
+    lat.init_fields(rho, u)
+    lat.step(g["T"], mode)            # alpha of the collisions at step T
+    omega = _vorticity(lat.moments()[1])
+    lat.step(1, mode)
+    return omega, lat.alpha_map()[0].astype(np.float64)
+
+
+def _blocks(a, b):
+    """Mean over b x b blocks of a square field."""
+    n = a.shape[0] // b
+    return a[:n * b, :n * b].reshape(n, b, n, b).mean(axis=(1, 3))
+
+
+def test_fig3_fig4_formula_vs_root_at_t1(elbm):
+    """Figs. 3-4 (t = 1, nu = 1e-5, 128^2): the formula and the bisection
+    give almost the same vortices, and the formula's alpha falls below 2
+    near the vortices and stays close to 2 elsewhere.  The figures' data is
+    not printed, so these are bands around the stated behaviour."""
+    wf, af = _run_to_t1(elbm, "formula")
+    wr, ar = _run_to_t1(elbm, "root")
+    out = {}
+    out["rel_l2"] = np.linalg.norm(wf - wr) / np.linalg.norm(wr)
+    out["corr"] = np.corrcoef(wf.ravel(), wr.ravel())[0, 1]
+    for b in (4, 8, 16):
+        out["corr_b%d" % b] = np.corrcoef(_blocks(wf, b).ravel(),
+                                          _blocks(wr, b).ravel())[0, 1]
+    out["enstrophy_ratio"] = np.mean(wf ** 2) / np.mean(wr ** 2)
+    dev = 2.0 - af
+    sm = np.abs(_blocks(wf, 4))
+    dev4 = _blocks(dev, 4)
+    hi = sm > np.quantile(sm, 0.9)
+    lo = sm < np.quantile(sm, 0.5)
+    out["dev_hi_over_lo_b4"] = dev4[hi].mean() / max(dev4[lo].mean(), 1e-300)
+    out["corr_dev_absw_b4"] = np.corrcoef(dev4.ravel(), sm.ravel())[0, 1]
+    out["share_alpha_lt2"] = np.mean(af < 2.0)
+    out["root_share_lt2"] = np.mean(ar < 2.0)
+    print("t=1:", {k: round(float(v), 4) for k, v in out.items()})
+    # pointwise the two runs drift apart (Re = 512000 on 128^2 amplifies
+    # the small alpha differences: correlation ~0.91), but at the scale of
+    # the vortices the shapes agree
+    assert out["corr_b8"] > 0.95 and out["corr_b16"] > 0.98
+    # the formula's alpha is at most the root (Eq. (9) lower bound), so it
+    # dissipates more: less enstrophy, by a bounded amount
+    assert 0.7 < out["enstrophy_ratio"] <= 1.0
+    # alpha deviates from 2 more where the flow is most vortical (measured
+    # 1.23x in the top tenth of 4 x 4 blocks over the calmer half)
+    assert out["dev_hi_over_lo_b4"] > 1.05
+    # and about half of the nodes need Eq. (9) (Fig. 5)
+    assert 0.3 < out["share_alpha_lt2"] < 0.7
