@@ -10,7 +10,25 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
+
 namespace elbm {
+
+// Raise a kernel's dynamic shared-memory limit once per device (the
+// attribute belongs to the device's context; `done` is per kernel
+// instantiation, one bit per device ordinal, safe under concurrent calls).
+template <class Kernel>
+static cudaError_t set_smem_limit(Kernel k, int bytes,
+                                  std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(
+      k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_release);
+  return e;
+}
 
 template <class Kernel>
 static int occupancy_grid(Kernel k, int block, long long threads_needed) {
@@ -66,11 +84,9 @@ static cudaError_t launch_sc32_one(const StepParams& p, int grid,
                                    cudaStream_t s, int* grid_used) {
   auto k = k_sc32<L, SHIFTED, DIAG, CHECK>;
   const int smem = 2 * L::Q * kSc32Threads * (int)sizeof(float);
-  static bool configured = false;   // per instantiation
-  if (!configured) {
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    configured = true;
-  }
+  static std::atomic<unsigned long long> configured{0};   // per instantiation
+  const cudaError_t se = set_smem_limit(k, smem, configured);
+  if (se != cudaSuccess) return se;
   if (grid <= 0) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
@@ -104,11 +120,9 @@ static cudaError_t launch_tma_one(const StepParams& p, int grid,
                                   cudaStream_t s, int* grid_used) {
   auto k = k_sc32_tma<L, DIAG, CHECK>;
   const int smem = kTmaStages * L::Q * kTmaRow * (int)sizeof(float);
-  static bool configured = false;   // per instantiation
-  if (!configured) {
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    configured = true;
-  }
+  static std::atomic<unsigned long long> configured{0};   // per instantiation
+  const cudaError_t se = set_smem_limit(k, smem, configured);
+  if (se != cudaSuccess) return se;
   if (grid <= 0) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
@@ -134,11 +148,9 @@ static cudaError_t launch_wide_one(const StepParams& p, int grid,
   auto k = k_sc32w<L, DIAG, CHECK>;
   const int smem =
       kWideWarps * 2 * wide_stage_floats<L>() * (int)sizeof(float);
-  static bool configured = false;   // per instantiation
-  if (!configured) {
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    configured = true;
-  }
+  static std::atomic<unsigned long long> configured{0};   // per instantiation
+  const cudaError_t se = set_smem_limit(k, smem, configured);
+  if (se != cudaSuccess) return se;
   if (grid <= 0) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
@@ -203,11 +215,9 @@ static cudaError_t launch_sc16_one(const StepParams& p, int grid,
                                    cudaStream_t s, int* grid_used) {
   auto k = k_sc16<L, DIAG, CHECK>;
   const int smem = 2 * L::Q * kSc32Threads * (int)sizeof(unsigned);
-  static bool configured = false;   // per instantiation
-  if (!configured) {
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    configured = true;
-  }
+  static std::atomic<unsigned long long> configured{0};   // per instantiation
+  const cudaError_t se = set_smem_limit(k, smem, configured);
+  if (se != cudaSuccess) return se;
   if (grid <= 0) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
