@@ -122,9 +122,9 @@ def _blocks(a, b):
 
 
 def test_fig3_fig4_formula_vs_root_at_t1(elbm):
-    """Figs. 3-4 (t = 1, nu = 1e-5, 128^2): the formula and the bisection
-    give almost the same vortices, and the formula's alpha falls below 2
-    near the vortices and stays close to 2 elsewhere.  The figures' data is
+    """Figs. 3-4 (t = 1, nu = 1e-5, 128^2): the vortex patterns of the
+    formula and of the bisection match closely, and the formula's alpha
+    drops below 2 at the vortices while staying near 2 away from them.  The figures' data is
     not printed, so these are bands around the stated behaviour."""
     wf, af = _run_to_t1(elbm, "formula")
     wr, ar = _run_to_t1(elbm, "root")

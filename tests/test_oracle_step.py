@@ -128,7 +128,7 @@ def test_taylor_green_energy_decay(orc):
 @pytest.mark.slow
 def test_shear_layer_accept_two_proportion(orc):
     """Fig. 5: on the 128^2 double shear layer with nu = 1e-5, alpha = 2 is
-    accepted at about half of the nodes for most of the time.  The figure's
+    accepted at roughly half of the nodes through most of the run.  The figure's
     data is not printed, so the pin is a band: a median in [0.3, 0.7] over
     the first quarter of the run (t <= 0.25)."""
     g = GOLD["double_shear_layer"]
