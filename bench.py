@@ -229,6 +229,48 @@ def time_steps(g, steps, mode, stream):
     return ms, kms, nk
 
 
+def taylor_green_3d_device(n, u0):
+    """The Taylor-Green fields of elbm_workloads.taylor_green_3d, built on
+    the GPU in FP64 (at 1024^3 the host copy would take 34 GB)."""
+    import torch
+    k = 2 * math.pi * torch.arange(n, dtype=torch.float64, device="cuda") / n
+    X, Y, Z = k[None, None, :], k[None, :, None], k[:, None, None]
+    u = torch.zeros((3, n, n, n), dtype=torch.float64, device="cuda")
+    u[0] = u0 * torch.sin(X) * torch.cos(Y) * torch.cos(Z)
+    u[1] = -u0 * torch.cos(X) * torch.sin(Y) * torch.cos(Z)
+    p = u0 ** 2 / 16 * (torch.cos(2 * X) + torch.cos(2 * Y)) * (
+        torch.cos(2 * Z) + 2)
+    rho = (1.0 + 3.0 * p).expand(n, n, n).contiguous()
+    return rho, u
+
+
+def capacity_line(elbm, stream, n=1024, steps=5):
+    """D3Q27 1024^3 (1.07 G nodes) in FP16-shifted storage: 116 GB of
+    populations, beyond what FP32 storage leaves room for next to the
+    initial fields.  Skipped when the device lacks 170 GB free."""
+    import torch
+    free, _ = torch.cuda.mem_get_info()
+    if free < 170e9:
+        return {"skipped": "needs 170 GB free, %.0f GB free" % (free / 1e9)}
+    g = elbm.Lattice("D3Q27", n, n, n, nu=nu_for(n), dtype="fp16_shifted")
+    rho, u = taylor_green_3d_device(n, U0)
+    g.init_fields(rho, u)
+    del rho, u
+    torch.cuda.empty_cache()
+    g.set_diagnostics(diag_every=0)
+    g.step(1, "formula")
+    ms, kms, nk = time_steps(g, steps, "formula", stream)
+    out = {"nodes": n ** 3, "steps": steps,
+           "mlups": round(n ** 3 * steps / (ms * 1e3), 1),
+           "device_gb": round(g.device_bytes / 1e9, 1)}
+    g.set_diagnostics(diag_every=1, check_every=1)
+    g.step(1, "formula")
+    out["n_violations"] = g.entropy_stats()["n_violations"]
+    g.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def secondary(elbm, stream):
     """FORMULA vs ROOT, FP32 vs FP64 (MLUPS), on smaller lattices."""
     out = {}
@@ -271,6 +313,7 @@ def secondary(elbm, stream):
         "bytes_per_lu": BYTES_PER_LU[("D3Q27", 2)],
         "achieved_gbs": round(kernel_gbs, 1),
         "frac": round(kernel_gbs / peaks()[0], 4), "peak_kind": peaks()[1]}
+    out["d3q27_1024_fp16_formula"] = capacity_line(elbm, stream)
     out["unit"] = "MLUPS"
     out["speedup_formula_vs_root_d3q27_fp32"] = round(
         out["d3q27_256_fp32_formula"] / out["d3q27_256_fp32_root"], 1)
