@@ -585,7 +585,11 @@ def e2e(elbm, args, n, nu, stream, world):
             "seconds": round(dt, 3),
             "phases_ms": {"init": round((t1 - t0) * 1e3, 1),
                           "steps": round((t2 - t1) * 1e3, 1),
-                          "readback": round((t3 - t2) * 1e3, 1)}}
+                          "readback": round((t3 - t2) * 1e3, 1)},
+            "host_pinned": {"inputs": bool(rho_h.is_pinned()
+                                           and u_h.is_pinned()),
+                            "outputs": bool(out_rho.is_pinned()
+                                            and out_u.is_pinned())}}
 
 
 def run_reference(args):
