@@ -75,11 +75,21 @@ void tune_cache_save() {
   fclose(f);
 }
 
+// Dynamic shared memory of k_batch: the gather stages and `cap` member
+// descriptors.
+int batch_smem(int tb, int cap) {
+  return 2 * 27 * tb * (int)sizeof(float) + cap * (int)sizeof(MemberDesc);
+}
+
+// Member-descriptor capacity staged for `count` members: a multiple of 16,
+// so that members joining a batch rarely change the launch's smem size.
+int desc_cap_for(int count) { return (count + 15) / 16 * 16; }
+
 template <int TB, int DIAG>
 cudaError_t launch_batch_kernel(const BatchParams& bp, int grid,
                                 cudaStream_t s) {
   auto k = k_batch<TB, DIAG>;
-  const int smem = 2 * 27 * TB * (int)sizeof(float);
+  const int smem = batch_smem(TB, bp.desc_cap);
   k<<<grid, TB, smem, s>>>(bp);
   count_launch();
   return cudaGetLastError();
@@ -104,21 +114,23 @@ cudaError_t launch_batch_fixup(int diag, const BatchParams& bp,
   return cudaGetLastError();
 }
 
-int max_blocks_per_sm(int tb) {
+int max_blocks_per_sm(int tb, int cap) {
   int per_sm = 0;
-  const int smem = 2 * 27 * tb * (int)sizeof(float);
+  // the attribute allows the largest table; the query uses this one
+  const int smem_max = batch_smem(tb, kBatchMaxMembers);
+  const int smem = batch_smem(tb, cap);
   if (tb == 128) {
     cudaFuncSetAttribute(k_batch<128, 0>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
     cudaFuncSetAttribute(k_batch<128, 1>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<128, 0>,
                                                   tb, smem);
   } else {
     cudaFuncSetAttribute(k_batch<256, 0>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
     cudaFuncSetAttribute(k_batch<256, 1>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<256, 0>,
                                                   tb, smem);
   }
@@ -180,6 +192,7 @@ struct elbm_batch {
   // graph cache
   cudaGraphExec_t exec = nullptr;
   int exec_burst = 0, exec_tb = 0, exec_grid = 0, exec_diag = -1;
+  int exec_cap = 0;   // member-descriptor capacity the graph was captured with
   size_t bytes = 0;
   long long bursts = 0;
   std::string err;
@@ -235,8 +248,8 @@ static elbm_status ensure_tables(elbm_batch* b) {
   cudaMemsetAsync(b->d_err, 0, 256, b->stream);
   cudaMemsetAsync(b->d_far_count, 0, 256, b->stream);
   // kernel attributes are set here, never during a graph capture
-  max_blocks_per_sm(128);
-  max_blocks_per_sm(256);
+  max_blocks_per_sm(128, 16);
+  max_blocks_per_sm(256, 16);
   return ELBM_OK;
 }
 
@@ -266,6 +279,7 @@ static BatchParams batch_params(elbm_batch* b) {
   bp.members = b->d_desc;
   bp.tile_begin = b->d_begin;
   bp.tile_member = b->d_tmem;
+  bp.desc_cap = desc_cap_for((int)b->h_desc.size());
   bp.count = b->d_count;
   bp.stats = b->d_stats;
   bp.far_queue = b->d_queue;
@@ -427,7 +441,7 @@ static elbm_status autotune(elbm_batch* b) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   for (int tb : {128, 256}) {
-    const int maxb = max_blocks_per_sm(tb);
+    const int maxb = max_blocks_per_sm(tb, desc_cap_for((int)b->h_desc.size()));
     for (int bps = 1; bps <= maxb; ++bps) {
       b->tb = tb;
       if (build_tables(b, 1, false, tb, true) == 0) break;
@@ -699,7 +713,8 @@ elbm_status elbm_batch_step(elbm_batch* b, long long nsteps) {
     cudaError_t e = cudaSuccess;
     if (b->use_graphs && steps_here == b->burst && b->burst > 1) {
       if (!b->exec || b->exec_burst != b->burst || b->exec_tb != b->tb ||
-          b->exec_grid != grid || b->exec_diag != (int)diag) {
+          b->exec_grid != grid || b->exec_diag != (int)diag ||
+          b->exec_cap != desc_cap_for(count)) {
         drop_graph(b);
         cudaStream_t cs;
         cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
@@ -724,6 +739,7 @@ elbm_status elbm_batch_step(elbm_batch* b, long long nsteps) {
                        std::string("graph capture: ") + cudaGetErrorString(e));
         b->exec_burst = b->burst;
         b->exec_tb = b->tb;
+        b->exec_cap = desc_cap_for(count);
         b->exec_grid = grid;
         b->exec_diag = diag;
       }

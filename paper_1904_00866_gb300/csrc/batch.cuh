@@ -25,7 +25,7 @@ namespace elbm {
 
 constexpr int kBatchMaxMembers = 256;
 
-struct MemberDesc {
+struct __align__(16) MemberDesc {
   float* buf[2];        // FP32-shifted pull-layout populations (select with
                         // pick(): a runtime index would force local memory)
   float* alpha_map;     // nullable
@@ -53,6 +53,8 @@ struct BatchParams {
   const MemberDesc* members;
   const unsigned* tile_begin;   // [count + 1] tile prefix of the members
   const unsigned char* tile_member;   // [tiles] member of each tile
+  int desc_cap;                 // member descriptors staged in shared memory
+                                // (>= count; fixes the launch's smem size)
   const int* count;             // members in the tile list
   MemberStats* stats;           // [kBatchMaxMembers]
   unsigned long long* far_queue;   // (member << 32) | node
@@ -152,10 +154,20 @@ __device__ __forceinline__ void batch_tile_stats(const Acc32& a,
 template <int TB, int DIAG>
 __global__ void __launch_bounds__(TB, 2048 / TB / 4)
     k_batch(const BatchParams bp) {
-  extern __shared__ float smem[];   // [2][27][TB]
+  extern __shared__ __align__(16) float smem[];   // [2][27][TB], descs
   __shared__ unsigned s_begin[kBatchMaxMembers + 1];
+  // the member descriptors are read on every tile: stage them in shared
+  // memory once (word copy; MemberDesc is trivially copyable)
+  MemberDesc* s_desc = reinterpret_cast<MemberDesc*>(smem + 2 * 27 * TB);
   const int count = *bp.count;
   for (int k = threadIdx.x; k <= count; k += TB) s_begin[k] = bp.tile_begin[k];
+  {
+    constexpr int W = (int)(sizeof(MemberDesc) / sizeof(unsigned));
+    const unsigned* src = reinterpret_cast<const unsigned*>(bp.members);
+    unsigned* dst = reinterpret_cast<unsigned*>(s_desc);
+    const int words = min(count, bp.desc_cap) * W;
+    for (int k = threadIdx.x; k < words; k += TB) dst[k] = src[k];
+  }
   __syncthreads();
   const unsigned total = s_begin[count];
   constexpr int kStage = 27 * TB;
@@ -163,7 +175,7 @@ __global__ void __launch_bounds__(TB, 2048 / TB / 4)
   unsigned tile = blockIdx.x;
   int stage = 0;
   auto issue = [&](unsigned t, int mi, float* sm) {
-    const MemberDesc m = bp.members[mi];   // by value: no reloads after stores
+    const MemberDesc m = s_desc[mi];   // by value: no reloads after stores
     if (bp.step >= m.steps_left) return;   // member finished in this burst
     const unsigned local = t - s_begin[mi];
     if (m.lattice == 1)
@@ -189,7 +201,7 @@ __global__ void __launch_bounds__(TB, 2048 / TB / 4)
     const int mi = mi_cur;
     mi_cur = mi_next;
     mi_next = mi_after;
-    const MemberDesc m = bp.members[mi];   // by value: no reloads after stores
+    const MemberDesc m = s_desc[mi];   // by value: no reloads after stores
     if (bp.step >= m.steps_left) continue;   // uniform per block
     const unsigned node = (tile - s_begin[mi]) * TB + threadIdx.x;
     const bool stats_step = DIAG && m.diag && bp.step == m.steps_left - 1;
