@@ -1,5 +1,5 @@
-"""Turbulent and transitional runs: FP32-shifted storage against the FP64
-path (itself pinned to the oracle at 1e-12 per population) through kinetic
+"""Turbulent and transitional runs: FP32- and FP16-shifted storage against
+the FP64 path (itself pinned to the oracle at 1e-12 per population) through kinetic
 energy and enstrophy histories, within 1 % at every sample -- the tolerance
 the method's precision target sets for turbulent cases.
 
@@ -54,7 +54,7 @@ def test_shear_layer_1024_fp32_vs_fp64_histories(elbm):
     nu = U * n / 30000.0
     rho, u = W.shear_layer(n, U=U)
     runs = {}
-    for dtype in ["fp64", "fp32_shifted"]:
+    for dtype in ["fp64", "fp32_shifted", "fp16_shifted"]:
         g = elbm.Lattice("D2Q9", n, n, 1, nu=nu, dtype=dtype)
         g.set_diagnostics(diag_every=1000, alpha_map_every=1000)
         g.init_fields(rho, u)
@@ -88,6 +88,12 @@ def test_shear_layer_1024_fp32_vs_fp64_histories(elbm):
                                  np.round(low64, 3).tolist(),
                                  np.round(low, 3).tolist()))
     assert de < 1e-2 and dz < 1e-2
+    e16, z16, _, _ = runs["fp16_shifted"]
+    de16 = np.abs(e16 / e64 - 1).max()
+    dz16 = np.abs(z16 / z64 - 1).max()
+    print("  FP16 storage: max rel dev energy %.2e, enstrophy %.2e"
+          % (de16, dz16))
+    assert de16 < 1e-2 and dz16 < 1e-2
 
 
 def test_taylor_green_re1600_fp32_vs_fp64_histories(elbm):
@@ -97,7 +103,7 @@ def test_taylor_green_re1600_fp32_vs_fp64_histories(elbm):
     tc = int(round(L / u0))
     rho, u = W.taylor_green_3d(n, u0)
     hist = {}
-    for dtype in ["fp64", "fp32_shifted"]:
+    for dtype in ["fp64", "fp32_shifted", "fp16_shifted"]:
         g = elbm.Lattice("D3Q27", n, n, n, nu=nu, dtype=dtype)
         g.set_diagnostics(diag_every=tc)
         g.init_fields(rho, u)
@@ -112,3 +118,9 @@ def test_taylor_green_re1600_fp32_vs_fp64_histories(elbm):
           "%.2e; enstrophy peak at %d t_c" % (de.max(), dz.max(),
                                                int(np.argmax(z64)) + 1))
     assert de.max() < 1e-2 and dz.max() < 1e-2
+    e16, z16 = hist["fp16_shifted"]
+    de16 = np.abs(e16 / e64 - 1).max()
+    dz16 = np.abs(z16 / z64 - 1).max()
+    print("  FP16 storage: max rel dev energy %.2e, enstrophy %.2e"
+          % (de16, dz16))
+    assert de16 < 1e-2 and dz16 < 1e-2
