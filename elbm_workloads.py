@@ -18,7 +18,10 @@ Workloads (all periodic, lattice units):
     above; u_y = delta sin(2 pi (x + 1/4)); rho = 1.
   * Random-phase low-mode flows (|k| <= kmax), divergence-free, rescaled to a
     given max |u|: 2D from a stream function, 3D as the curl of a vector
-    potential.
+    potential; in 1D a random low-mode density and velocity profile.
+  * Shock tube of the paper's first experiment: a density step at rest on
+    the nodes 0..nodes, with zero-gradient ends realised by even reflection
+    into a periodic row of 2 (nodes + 1) nodes.
 """
 import math
 
@@ -86,6 +89,33 @@ def uniform_flow(shape, u, rho0=1.0):
     rho = np.full(shape, rho0)
     uu = np.stack([np.full(shape, float(c)) for c in u])
     return rho, uu
+
+
+def shock_tube(nodes=800, rho_left=1.5, rho_right=0.75, split=400):
+    """Density step at rest on x = 0..nodes (rho_left for x <= split), mirrored
+    onto x = nodes + 1 .. 2 nodes + 1 so that the periodic row of
+    2 (nodes + 1) nodes has zero-gradient ends at x = 0 and x = nodes.
+    Returns rho (1, 1, n), u (1, 1, 1, n)."""
+    n = 2 * (nodes + 1)
+    x = np.arange(n)
+    rho = np.where((x <= split) | (x >= n - 1 - split), rho_left, rho_right)
+    return rho.astype(np.float64).reshape(1, 1, n), np.zeros((1, 1, 1, n))
+
+
+def random_phase_1d(n, seed, kmax=4, umax=0.05, drho=0.05):
+    """Random low-mode periodic row: rho = 1 + drho s(x) and u = umax v(x),
+    s and v sums of modes 1..kmax with random phases, scaled to max |s| =
+    max |v| = 1.  Returns rho (1, 1, n), u (1, 1, 1, n)."""
+    rng = np.random.default_rng(seed)
+    t = 2 * math.pi * np.arange(n) / n
+    out = []
+    for _ in range(2):
+        a = rng.standard_normal(kmax)
+        ph = rng.uniform(0, 2 * math.pi, kmax)
+        v = sum(a[k] * np.cos((k + 1) * t + ph[k]) for k in range(kmax))
+        out.append(v / np.abs(v).max())
+    rho = 1.0 + drho * out[0]
+    return rho.reshape(1, 1, n), (umax * out[1]).reshape(1, 1, 1, n)
 
 
 def random_phase_2d(n, seed, kmax=4, umax=0.05, ny=None):

@@ -62,7 +62,11 @@ extern "C" {
 
 typedef struct elbm_handle elbm_handle;
 
-typedef enum { ELBM_D2Q9 = 0, ELBM_D3Q27 = 1 } elbm_lattice;
+/* Velocity sets: D2Q9 and D3Q27 are tensor products of D1Q3 (velocities
+ * {0, +1, -1}, weights {2/3, 1/6, 1/6}); D1Q3 itself serves one-dimensional
+ * problems such as the shock tube of Fig. 2 (nx nodes, ny = nz = 1, FP64
+ * storage only; the batched and static entry points take D2Q9 and D3Q27). */
+typedef enum { ELBM_D2Q9 = 0, ELBM_D3Q27 = 1, ELBM_D1Q3 = 2 } elbm_lattice;
 
 /* Storage (and arithmetic) of the populations.
  *   ELBM_FP64          f_i in FP64, FP64 arithmetic throughout.
@@ -133,9 +137,11 @@ typedef struct {
   double alpha_dev_max;     /* max |alpha - alpha_FORMULA in FP64|        */
 } elbm_entropy_stats_t;
 
-/* Create a handle for a periodic nx x ny x nz lattice (nz = 1 for D2Q9) of
- * viscosity nu > 0 (beta from Eq. (2)).  No device memory is touched until
- * elbm_init_fields / elbm_set_populations.  *out is NULL on failure. */
+/* Create a handle for a periodic nx x ny x nz lattice (nz = 1 for D2Q9,
+ * ny = nz = 1 for D1Q3) of viscosity nu > 0 (beta from Eq. (2)).  A D1Q3
+ * handle with another storage than ELBM_FP64 is ELBM_EINVAL.  No device
+ * memory is touched until elbm_init_fields / elbm_set_populations.  *out is
+ * NULL on failure. */
 ELBM_API elbm_status elbm_create(elbm_handle **out, elbm_lattice lattice, int nx,
                         int ny, int nz, double nu, elbm_dtype dtype);
 
@@ -219,8 +225,8 @@ ELBM_API elbm_status elbm_alpha_map(elbm_handle *h, float *alpha_out);
 ELBM_API elbm_status elbm_entropy_stats(elbm_handle *h, elbm_entropy_stats_t *out);
 
 /* Enstrophy 1/2 <|omega|^2> of f^n: omega = curl u by second-order central
- * differences on the periodic lattice (2D: omega_z), averaged over nodes.
- * Synchronises. */
+ * differences on the periodic lattice (2D: omega_z), averaged over nodes;
+ * 0 for D1Q3, whose velocity field has no curl.  Synchronises. */
 ELBM_API elbm_status elbm_enstrophy(elbm_handle *h, double *out);
 
 /* Steps taken since the last initialisation. */

@@ -23,15 +23,15 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libelbm.so")
 
-D2Q9, D3Q27 = 0, 1
+D2Q9, D3Q27, D1Q3 = 0, 1, 2
 FP64, FP32, FP32_SHIFTED, FP16_SHIFTED = 0, 1, 2, 3
 FORMULA, ROOT, SECANT = 0, 1, 2
-LATTICES = {"D2Q9": D2Q9, "D3Q27": D3Q27}
+LATTICES = {"D2Q9": D2Q9, "D3Q27": D3Q27, "D1Q3": D1Q3}
 DTYPES = {"fp64": FP64, "fp32": FP32, "fp32_shifted": FP32_SHIFTED,
           "fp16_shifted": FP16_SHIFTED}
 MODES = {"formula": FORMULA, "root": ROOT, "secant": SECANT}
-Q = {D2Q9: 9, D3Q27: 27}
-DIM = {D2Q9: 2, D3Q27: 3}
+Q = {D2Q9: 9, D3Q27: 27, D1Q3: 3}
+DIM = {D2Q9: 2, D3Q27: 3, D1Q3: 1}
 
 STATUS = {0: "ELBM_OK", 1: "ELBM_EINVAL", 2: "ELBM_ENOMEM", 3: "ELBM_ECUDA",
           4: "ELBM_ENONFINITE", 5: "ELBM_ENEGATIVE", 6: "ELBM_EROOT_CAP",
@@ -196,8 +196,8 @@ def _torch_cuda():
 class Lattice:
     """One periodic lattice advanced on the GPU.
 
-    lattice: "D2Q9" | "D3Q27"; dtype: "fp64" | "fp32" | "fp32_shifted" |
-    "fp16_shifted";
+    lattice: "D2Q9" | "D3Q27" | "D1Q3" (FP64 only); dtype: "fp64" | "fp32" |
+    "fp32_shifted" | "fp16_shifted";
     allocator: "torch" (PyTorch caching allocator, the default when PyTorch
     sees a GPU) or "cuda" (cudaMalloc inside the library).
     """

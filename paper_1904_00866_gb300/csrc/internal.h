@@ -52,4 +52,8 @@ ELBM_DECLARE_LAUNCHERS(d2q9)
 ELBM_DECLARE_LAUNCHERS(d3q27)
 #undef ELBM_DECLARE_LAUNCHERS
 
+cudaError_t launch_fp64_d1q3(int mode, int diag, int check,
+                             const StepParams& p, int grid, int block,
+                             cudaStream_t s, int* grid_used);
+
 }  // namespace elbm

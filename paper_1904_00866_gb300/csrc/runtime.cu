@@ -264,11 +264,14 @@ static int grid_for(long long n) {
   return (int)(g < cap ? (g < 1 ? 1 : g) : cap);
 }
 
-// Dispatch a node-parallel helper kernel on (lattice, storage type).
+// Dispatch a node-parallel helper kernel on (lattice, storage type); D1Q3
+// handles hold FP64 storage only.
 #define DISPATCH_LT(h, KERNEL, ...)                                          \
   do {                                                                       \
     const int grid_ = grid_for((h)->n);                                      \
-    if ((h)->lattice == ELBM_D2Q9) {                                         \
+    if ((h)->lattice == ELBM_D1Q3) {                                         \
+      KERNEL<D1Q3, double><<<grid_, 256, 0, (h)->stream>>>(__VA_ARGS__);     \
+    } else if ((h)->lattice == ELBM_D2Q9) {                                  \
       if ((h)->dtype == ELBM_FP64)                                           \
         KERNEL<D2Q9, double><<<grid_, 256, 0, (h)->stream>>>(__VA_ARGS__);   \
       else if ((h)->dtype == ELBM_FP16_SHIFTED)                              \
@@ -310,7 +313,7 @@ elbm_status elbm_create(elbm_handle** out, elbm_lattice lattice, int nx,
                         int ny, int nz, double nu, elbm_dtype dtype) {
   if (!out) return fail(nullptr, ELBM_EINVAL, "out is NULL");
   *out = nullptr;
-  if (lattice != ELBM_D2Q9 && lattice != ELBM_D3Q27)
+  if (lattice != ELBM_D2Q9 && lattice != ELBM_D3Q27 && lattice != ELBM_D1Q3)
     return fail(nullptr, ELBM_EINVAL, "unknown lattice");
   if (dtype != ELBM_FP64 && dtype != ELBM_FP32 && dtype != ELBM_FP32_SHIFTED &&
       dtype != ELBM_FP16_SHIFTED)
@@ -319,10 +322,14 @@ elbm_status elbm_create(elbm_handle** out, elbm_lattice lattice, int nx,
     return fail(nullptr, ELBM_EINVAL, "lattice dimensions must be >= 1");
   if (lattice == ELBM_D2Q9 && nz != 1)
     return fail(nullptr, ELBM_EINVAL, "D2Q9 needs nz == 1");
+  if (lattice == ELBM_D1Q3 && (ny != 1 || nz != 1))
+    return fail(nullptr, ELBM_EINVAL, "D1Q3 needs ny == nz == 1");
+  if (lattice == ELBM_D1Q3 && dtype != ELBM_FP64)
+    return fail(nullptr, ELBM_EINVAL, "D1Q3 supports FP64 storage only");
   if (!(nu > 0.0) || !(nu < 1e6))
     return fail(nullptr, ELBM_EINVAL, "nu must be > 0");
   const long long n = (long long)nx * ny * nz;
-  const int q = lattice == ELBM_D2Q9 ? 9 : 27;
+  const int q = lattice == ELBM_D1Q3 ? 3 : (lattice == ELBM_D2Q9 ? 9 : 27);
   if (n > 0xffffffffLL || (long long)q * n > (1LL << 40))
     return fail(nullptr, ELBM_EINVAL, "lattice too large");
   elbm_handle* h = new elbm_handle();
@@ -331,7 +338,7 @@ elbm_status elbm_create(elbm_handle** out, elbm_lattice lattice, int nx,
   h->ny = ny;
   h->nz = nz;
   h->q = q;
-  h->d = lattice == ELBM_D2Q9 ? 2 : 3;
+  h->d = lattice == ELBM_D1Q3 ? 1 : (lattice == ELBM_D2Q9 ? 2 : 3);
   h->n = n;
   h->nu = nu;
   const double cs2 = 1.0 / 3.0;
@@ -576,7 +583,9 @@ elbm_status elbm_step(elbm_handle* h, long long nsteps, elbm_alpha_mode mode) {
       ev = &h->events[h->events_used++];
       cudaEventRecord(ev->first, h->stream);
     }
-    if (storage == 0)
+    if (h->lattice == ELBM_D1Q3)
+      e = launch_fp64_d1q3(mode, diag, check, p, 0, 256, h->stream, &grid);
+    else if (storage == 0)
       e = d2 ? launch_fp64_d2q9(mode, diag, check, p, 0, 256, h->stream, &grid)
              : launch_fp64_d3q27(mode, diag, check, p, 0, 256, h->stream, &grid);
     else if (fp32_formula && storage == 2)
@@ -732,6 +741,10 @@ elbm_status elbm_enstrophy(elbm_handle* h, double* out) {
   if (!h->allocated) return fail(h, ELBM_ESTATE, "fields not initialised");
   elbm_status st = check_errors(h);
   if (st) return st;
+  if (h->d == 1) {   // a one-dimensional velocity field has no curl
+    *out = 0.0;
+    return ELBM_OK;
+  }
   double* tmp = fields_staging(h);
   if (!tmp) return fail(h, ELBM_ENOMEM, "staging allocation failed");
   Geo g = geo(h);

@@ -69,6 +69,15 @@ def test_create_validates_arguments_without_gpu(elbm):
     assert L.elbm_set_diagnostics(h, -1, 0, 0, 4) == 1
     assert L.elbm_set_diagnostics(h, 1, 0, 0, 4) == 0
     L.elbm_destroy(h)
+    # D1Q3: one row of nodes, FP64 storage only
+    assert L.elbm_create(ctypes.byref(h), 2, 8, 2, 1, 0.01, 0) == 1
+    assert L.elbm_create(ctypes.byref(h), 2, 8, 1, 2, 0.01, 0) == 1
+    for dtype in (1, 2, 3):
+        assert L.elbm_create(ctypes.byref(h), 2, 8, 1, 1, 0.01, dtype) == 1
+        assert b"FP64" in L.elbm_last_error(None)
+    assert L.elbm_create(ctypes.byref(h), 2, 1602, 1, 1, 1e-5, 0) == 0
+    assert L.elbm_step(h, 1, 0) == 7
+    L.elbm_destroy(h)
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):

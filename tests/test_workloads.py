@@ -97,3 +97,23 @@ def test_request_stream_is_poisson_at_the_stated_rate():
     steps = np.array([r["steps"] for r in reqs])
     assert steps.min() >= 100 and steps.max() <= 10000
     assert 0.4 < np.mean([r["lattice"] == "D2Q9" for r in reqs]) < 0.6
+
+
+def test_shock_tube_is_an_even_reflection_of_the_step():
+    rho, u = W.shock_tube(800, 1.5, 0.75, 400)
+    n = rho.size
+    assert n == 1602 and rho.shape == (1, 1, n) and u.shape == (1, 1, 1, n)
+    r = rho.ravel()
+    assert np.all(r[:401] == 1.5) and np.all(r[401:801] == 0.75)
+    # mirror image about the midpoint between x = 800 and x = 801: the
+    # periodic row has zero-gradient ends at x = 0 and x = 800
+    assert np.array_equal(r[801:], r[800::-1])
+    assert np.all(u == 0.0)
+
+
+def test_random_phase_1d_ranges_and_seed():
+    rho, u = W.random_phase_1d(97, seed=2, umax=0.1, drho=0.05)
+    assert rho.shape == (1, 1, 97) and u.shape == (1, 1, 1, 97)
+    assert abs(np.abs(rho - 1).max() - 0.05) < 1e-15
+    assert abs(np.abs(u).max() - 0.1) < 1e-15
+    assert np.array_equal(u, W.random_phase_1d(97, seed=2, umax=0.1)[1])
