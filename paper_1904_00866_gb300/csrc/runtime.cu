@@ -12,6 +12,7 @@
 #include "../../include/elbm.h"
 #include "internal.h"
 #include "io_kernels.cuh"
+#include "lattice_d1q3.cuh"
 
 namespace elbm {
 
