@@ -21,7 +21,7 @@ Workloads (all periodic, lattice units):
     potential; in 1D a random low-mode density and velocity profile.
   * Shock tube of the paper's first experiment: a density step at rest on
     the nodes 0..nodes, with zero-gradient ends realised by even reflection
-    into a periodic row of 2 (nodes + 1) nodes.
+    into a periodic row of 2 (nodes + 1) nodes, or with periodic ends.
 """
 import math
 
@@ -91,14 +91,25 @@ def uniform_flow(shape, u, rho0=1.0):
     return rho, uu
 
 
-def shock_tube(nodes=800, rho_left=1.5, rho_right=0.75, split=400):
-    """Density step at rest on x = 0..nodes (rho_left for x <= split), mirrored
-    onto x = nodes + 1 .. 2 nodes + 1 so that the periodic row of
-    2 (nodes + 1) nodes has zero-gradient ends at x = 0 and x = nodes.
+def shock_tube(nodes=800, rho_left=1.5, rho_right=0.75, split=400,
+               ends="zero_gradient"):
+    """Density step at rest on x = 0..nodes (rho_left for x <= split).
+
+    ends="zero_gradient": the row is mirrored onto x = nodes + 1 .. 2 nodes + 1
+    so that the periodic row of 2 (nodes + 1) nodes has zero-gradient ends
+    at x = 0 and x = nodes.  ends="periodic": the nodes + 1 nodes wrap
+    around, so a second step (rho_right | rho_left) sits at the wrap.
     Returns rho (1, 1, n), u (1, 1, 1, n)."""
-    n = 2 * (nodes + 1)
-    x = np.arange(n)
-    rho = np.where((x <= split) | (x >= n - 1 - split), rho_left, rho_right)
+    if ends == "periodic":
+        n = nodes + 1
+        rho = np.where(np.arange(n) <= split, rho_left, rho_right)
+    elif ends == "zero_gradient":
+        n = 2 * (nodes + 1)
+        x = np.arange(n)
+        rho = np.where((x <= split) | (x >= n - 1 - split), rho_left,
+                       rho_right)
+    else:
+        raise ValueError("ends must be 'zero_gradient' or 'periodic'")
     return rho.astype(np.float64).reshape(1, 1, n), np.zeros((1, 1, 1, n))
 
 

@@ -109,6 +109,9 @@ def test_shock_tube_is_an_even_reflection_of_the_step():
     # periodic row has zero-gradient ends at x = 0 and x = 800
     assert np.array_equal(r[801:], r[800::-1])
     assert np.all(u == 0.0)
+    rho, u = W.shock_tube(800, 1.5, 0.75, 400, ends="periodic")
+    r = rho.ravel()
+    assert r.size == 801 and np.all(r[:401] == 1.5) and np.all(r[401:] == 0.75)
 
 
 def test_random_phase_1d_ranges_and_seed():
