@@ -35,3 +35,12 @@ def test_reference_arm_prints_one_comparable_line():
 def test_reference_arm_follows_the_storage_option():
     d = _line("--storage", "fp16_shifted")
     assert d["metric"] == "MLUPS (D3Q27 FORMULA FP16-shifted)"
+
+
+def test_cpu_baseline_reports_all_cores_and_one_thread():
+    import bench
+    d = bench.cpu_baseline(target_s=0.2, single_s=0.2, n=16)
+    assert d["kind"] == "oracle" and d["unit"] == "MLUPS"
+    assert d["value"] > 0 and d["single_thread"] > 0
+    assert d["cores"] == (os.cpu_count() or 1)
+    assert "16^3" in d["sample"]
