@@ -300,7 +300,7 @@ ELBM_API elbm_status elbm_step_static(elbm_lattice lattice, int nx, int ny,
 typedef struct elbm_batch elbm_batch;
 
 typedef struct {
-  elbm_lattice lattice;
+  elbm_lattice lattice; /* ELBM_D2Q9 or ELBM_D3Q27 (D1Q3: ELBM_EINVAL) */
   int nx, ny, nz;      /* nz = 1 for D2Q9 */
   double nu;           /* > 0; beta from Eq. (2) */
 } elbm_member_spec;

@@ -567,7 +567,9 @@ elbm_status elbm_batch_add(elbm_batch* b, const elbm_member_spec* spec,
     return bfail(b, ELBM_EINVAL, "NULL argument");
   *id_out = -1;
   if (spec->lattice != ELBM_D2Q9 && spec->lattice != ELBM_D3Q27)
-    return bfail(b, ELBM_EINVAL, "unknown lattice");
+    return bfail(b, ELBM_EINVAL, spec->lattice == ELBM_D1Q3
+                                     ? "batch members are D2Q9 or D3Q27"
+                                     : "unknown lattice");
   if (spec->nx < 1 || spec->ny < 1 || spec->nz < 1 ||
       (spec->lattice == ELBM_D2Q9 && spec->nz != 1))
     return bfail(b, ELBM_EINVAL, "invalid lattice dimensions");

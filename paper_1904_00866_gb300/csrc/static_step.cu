@@ -56,7 +56,9 @@ extern "C" elbm_status elbm_step_static(
     const float* f_in_device, float* f_out_device, float* alpha_out_device,
     void* cuda_stream, elbm_entropy_stats_t* stats_out) {
   if (lattice != ELBM_D2Q9 && lattice != ELBM_D3Q27)
-    return fail(ELBM_EINVAL, "unknown lattice");
+    return fail(ELBM_EINVAL, lattice == ELBM_D1Q3
+                                 ? "elbm_step_static takes D2Q9 and D3Q27 only"
+                                 : "unknown lattice");
   if (nx < 1 || ny < 1 || nz < 1 || (lattice == ELBM_D2Q9 && nz != 1))
     return fail(ELBM_EINVAL, "invalid lattice dimensions");
   const long long n = (long long)nx * ny * nz;

@@ -80,6 +80,24 @@ def test_create_validates_arguments_without_gpu(elbm):
     L.elbm_destroy(h)
 
 
+def test_batch_and_static_entry_points_reject_d1q3_without_gpu(elbm):
+    L = elbm.lib()
+    st = L.elbm_step_static(2, 64, 1, 1, 1e-4, 1.0, None, None, None, None,
+                            None)
+    assert st == 1 and b"D2Q9 and D3Q27" in L.elbm_last_error(None)
+    b = ctypes.c_void_p()
+    assert L.elbm_batch_create(ctypes.byref(b), 4) == 0
+    spec = elbm.MemberSpec(lattice=2, nx=64, ny=1, nz=1, nu=1e-4)
+    rho = (ctypes.c_double * 64)(*([1.0] * 64))
+    u = (ctypes.c_double * 64)()
+    mid = ctypes.c_int(7)
+    assert L.elbm_batch_add(b, ctypes.byref(spec), rho, u,
+                            ctypes.byref(mid)) == 1
+    assert mid.value == -1
+    assert b"D2Q9 or D3Q27" in L.elbm_batch_last_error(b)
+    L.elbm_batch_destroy(b)
+
+
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     import paper_1904_00866_gb300 as e
     monkeypatch.setattr(e, "_lib", None)
