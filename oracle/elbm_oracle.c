@@ -24,6 +24,9 @@
  *   alpha_secant         the modified secant iteration of the conclusion
  *   orc_collide_node     Eq. (1) = Eq. (5a) at one node
  *   orc_step             Eq. (5a) at every node, then Eq. (5b) (periodic)
+ *   orc_enstrophy        1/2 <|curl u|^2> by central differences (the
+ *                        diagnostic of the Taylor-Green histories; not in the
+ *                        paper), pinned to closed forms for single-mode flows
  */
 #include "elbm_oracle.h"
 
