@@ -103,7 +103,9 @@ typedef enum {
   ELBM_ECUDA = 3,       /* CUDA runtime error (message in elbm_last_error) */
   ELBM_ENONFINITE = 4,  /* a node had NaN/Inf moments or |u_a| >= 1        */
   ELBM_ENEGATIVE = 5,   /* a node had a population <= 0                    */
-  ELBM_EROOT_CAP = 6,   /* reserved                                        */
+  ELBM_EROOT_CAP = 6,   /* ROOT bisection stopped at its iteration cap at
+                           one or more nodes of the reported step (returned
+                           by elbm_entropy_stats after filling *out)       */
   ELBM_ESTATE = 7       /* call not valid in the handle's state            */
 } elbm_status;
 
@@ -119,10 +121,11 @@ typedef struct {
   long long n_accept_two;   /* alpha_* = 2 accepted (Fig. 5 counter)      */
   long long n_accept_star;  /* alpha_* accepted (any alpha_*)             */
   long long n_formula;      /* Eq. (9) / secant / root alpha used         */
-  long long n_band;         /* FP32 FORMULA: sign of Delta H(2) not
-                               certified, conservative Eq. (9) chord used  */
+  long long n_band;         /* FP32 FORMULA: FP32 decision not certified,
+                               decided by the double-float second stage   */
   long long n_far;          /* FP32 FORMULA: node solved in FP64 (far from
-                               equilibrium)                               */
+                               equilibrium, invalid, or undecided by the
+                               second stage)                              */
   long long n_degenerate;   /* f^eq == f: alpha = 2                       */
   long long n_root_iters;   /* ROOT/SECANT iterations                     */
   long long n_root_cap;     /* ROOT stopped at the iteration cap          */
@@ -193,19 +196,25 @@ ELBM_API elbm_status elbm_set_populations(elbm_handle *h, const double *f);
  * Asynchronous on the handle's stream.
  * FP32 FORMULA: Delta H(2) and Delta H(1) are evaluated in FP32 from the
  * moments sum_i f_i x_i^k (k = 2..4, or 2..8 when max|x_i| > 1/100) with a
- * bound E on their error; alpha = 2 is accepted only when Delta H(2) + E
- * <= 0, otherwise alpha is the Eq. (9) chord evaluated on the upper bounds
- * and rounded down, or 1 where neither sign is resolved in FP32 (including
- * nodes whose f^eq - f is zero in FP32), so H(f*(alpha)) <= H(f) holds for
- * the stored state; nodes with max|x_i| > 1/8, |u_a| >= 1/2 or invalid
- * populations are solved in FP64. */
+ * bound E on their error.  alpha = 2 is accepted when Delta H(2) + E <= 0
+ * (the acceptance test after Eq. (8)); the Eq. (9) chord, evaluated on the
+ * upper bounds and rounded down, is taken when Delta H(2) - E > 0 and
+ * Delta H(1) + E < 0.  A node where either sign lies within E is
+ * recomputed in double-float arithmetic (f^eq - f to about 1e-12 of f) and
+ * decided again with that smaller error; the rare node still undecided is
+ * solved in FP64.  So each node takes the branch of the exact arithmetic
+ * and H(f*(alpha)) <= H(f) holds for the stored state.  Nodes with
+ * max|x_i| > 1/8, |u_a| >= 1/2 or invalid populations are solved in FP64.
+ * FP32 and FP16 storages take fewer than 2^31 nodes. */
 ELBM_API elbm_status elbm_step(elbm_handle *h, long long nsteps, elbm_alpha_mode mode);
 
 /* Block until the handle's queued work is done; reports flagged errors. */
 ELBM_API elbm_status elbm_sync(elbm_handle *h);
 
-/* Density [nz][ny][nx] and velocity [d][nz][ny][nx] of f^n (host, FP64).
- * Either pointer may be NULL.  Synchronises. */
+/* Density [nz][ny][nx] and velocity [d][nz][ny][nx] of f^n (host, FP64):
+ * rho = sum_i f_i and rho u = sum_i c_i f_i, the mass and momentum moments
+ * that the equilibrium of Eq. (3) conserves (the constraints stated after
+ * Eq. (3)).  Either pointer may be NULL.  Synchronises. */
 ELBM_API elbm_status elbm_moments(elbm_handle *h, double *rho_out, double *u_out);
 
 /* Populations f^n as FP64 [Q][nz][ny][nx] (host).  Synchronises. */
@@ -217,11 +226,19 @@ ELBM_API elbm_status elbm_get_populations_nodes(elbm_handle *h, const long long 
                                        int count, double *f_out);
 
 /* Per-node alpha [nz][ny][nx] (FP32, host) of the last step that wrote the
- * alpha map (ELBM_ESTATE if none did).  Synchronises. */
+ * alpha map (ELBM_ESTATE if none did): the relaxation parameter of Eq. (1)
+ * chosen by the step's alpha mode, the field the paper shows for the
+ * double shear layer in Fig. 4.  Synchronises. */
 ELBM_API elbm_status elbm_alpha_map(elbm_handle *h, float *alpha_out);
 
-/* Diagnostics of the last step that computed them (ELBM_ESTATE if none).
- * Synchronises. */
+/* Diagnostics of the last step that computed them (ELBM_ESTATE if none):
+ * mass, momentum and kinetic energy of f^n; the total entropy of Eq. (3)
+ * and the count of nodes whose collision raised H beyond rounding (the
+ * local H-theorem of Eq. (7), whose sum over the lattice is Eq. (6)); the
+ * count of nodes accepting alpha = 2 (the proportion plotted in Fig. 5);
+ * and the alpha-selection counters.  Synchronises.  Returns
+ * ELBM_EROOT_CAP, with *out filled, when ROOT bisection stopped at its
+ * iteration cap at one or more nodes of that step. */
 ELBM_API elbm_status elbm_entropy_stats(elbm_handle *h, elbm_entropy_stats_t *out);
 
 /* Enstrophy 1/2 <|omega|^2> of f^n: omega = curl u by second-order central
@@ -278,7 +295,10 @@ ELBM_API elbm_status elbm_profile(elbm_handle *h, double *stream_collide_ms,
  * serialised by the caller.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress); make that first call
  * before any stream capture.  Errors: ELBM_EINVAL for invalid arguments or
- * sizes, ELBM_ECUDA for CUDA errors; the message is elbm_last_error(NULL).
+ * sizes (checked before anything is queued), ELBM_ECUDA for CUDA errors and,
+ * when stats_out is given, for a kernel whose bounded wait ran out (the
+ * opt-in bulk-copy variant selected by ELBM_SC32_VARIANT=tma); the message
+ * is elbm_last_error(NULL).
  * No cudaMalloc, cudaFree or allocating library call is made. */
 ELBM_API elbm_status elbm_step_static(elbm_lattice lattice, int nx, int ny,
                                       int nz, double nu, double rho0,
@@ -363,6 +383,10 @@ ELBM_API size_t elbm_batch_device_bytes(const elbm_batch *b);
 
 /* Reference density rho0 of the shifted storage (meaningful after init). */
 ELBM_API double elbm_rho0(const elbm_handle *h);
+
+/* The beta of Eq. (2) the handle's steps use, c_s^2 / (2 nu + c_s^2) with
+ * dt = 1 and c_s^2 = 1/3 (NaN for a NULL handle).  Needs no device. */
+ELBM_API double elbm_beta(const elbm_handle *h);
 
 #ifdef __cplusplus
 }

@@ -33,6 +33,7 @@ MODES = {"formula": FORMULA, "root": ROOT, "secant": SECANT}
 Q = {D2Q9: 9, D3Q27: 27, D1Q3: 3}
 DIM = {D2Q9: 2, D3Q27: 3, D1Q3: 1}
 
+EROOT_CAP = 6
 STATUS = {0: "ELBM_OK", 1: "ELBM_EINVAL", 2: "ELBM_ENOMEM", 3: "ELBM_ECUDA",
           4: "ELBM_ENONFINITE", 5: "ELBM_ENEGATIVE", 6: "ELBM_EROOT_CAP",
           7: "ELBM_ESTATE"}
@@ -122,6 +123,7 @@ SIGNATURES = {
     "elbm_device_bytes": (ctypes.c_size_t, [_P]),
     "elbm_launch_count": (ctypes.c_longlong, []),
     "elbm_rho0": (ctypes.c_double, [_P]),
+    "elbm_beta": (ctypes.c_double, [_P]),
     "elbm_step_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_int,
                                         ctypes.c_double, ctypes.c_double, _P,
@@ -334,8 +336,17 @@ class Lattice:
         return a
 
     def entropy_stats(self):
+        """Statistics of the last diagnostic step.  A step where ROOT
+        bisection hit its iteration cap still returns its statistics (with
+        n_root_cap > 0) and raises a RuntimeWarning."""
         s = EntropyStats()
-        self._check(lib().elbm_entropy_stats(self._h, ctypes.byref(s)))
+        st = lib().elbm_entropy_stats(self._h, ctypes.byref(s))
+        if st == EROOT_CAP:
+            import warnings
+            warnings.warn(lib().elbm_last_error(self._h).decode(),
+                          RuntimeWarning)
+        else:
+            self._check(st)
         return s.as_dict()
 
     def enstrophy(self):
@@ -369,8 +380,8 @@ class Lattice:
 
     @property
     def beta(self):
-        cs2 = 1.0 / 3.0
-        return cs2 / (2.0 * self.nu + cs2)
+        """The relaxation factor beta the library steps with."""
+        return lib().elbm_beta(self._h)
 
 
 class Batch:

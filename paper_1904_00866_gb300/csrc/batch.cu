@@ -173,7 +173,9 @@ struct elbm_batch {
   size_t tmem_cap = 0;
   int* d_count = nullptr;
   MemberStats* d_stats = nullptr;
-  unsigned* d_far_count = nullptr;
+  unsigned* d_far_count = nullptr;   // [0..1] deferred, [2..3] undecided
+  float* d_refine = nullptr;         // undecided-node buffer
+  unsigned refine_cap = 0;
   unsigned* d_err = nullptr;
   unsigned long long* d_queue = nullptr;
   size_t queue_cap = 0;
@@ -271,6 +273,15 @@ static elbm_status ensure_queue(elbm_batch* b) {
   b->d_queue = (unsigned long long*)balloc(b, cap * sizeof(unsigned long long));
   if (!b->d_queue) return bfail(b, ELBM_ENOMEM, "far queue allocation failed");
   b->queue_cap = cap;
+  // undecided-node buffer: a sixteenth of the queue, at least 65,536
+  // entries (a full buffer falls back to the gathering queue)
+  bfree(b, b->d_refine,
+        sizeof(float) * kBatchRefineRows * (size_t)b->refine_cap);
+  const size_t rcap =
+      std::min<size_t>(0xffffffffu, std::max<size_t>(cap / 16, 65536));
+  b->d_refine =
+      (float*)balloc(b, sizeof(float) * kBatchRefineRows * rcap);
+  b->refine_cap = b->d_refine ? (unsigned)rcap : 0u;
   return ELBM_OK;
 }
 
@@ -285,6 +296,9 @@ static BatchParams batch_params(elbm_batch* b) {
   bp.far_queue = b->d_queue;
   bp.far_cap = (unsigned)std::min<size_t>(b->queue_cap, 0xffffffffu);
   bp.far_count = b->d_far_count;
+  bp.refine_buf = b->d_refine;
+  bp.refine_cap = b->refine_cap;
+  bp.refine_count = b->d_far_count + 2;
   bp.err_flags = b->d_err;
   bp.step = 0;
   return bp;
@@ -364,7 +378,7 @@ static elbm_status upload_tables(elbm_batch* b) {
     e = cudaMemcpyAsync(b->d_count, &count, sizeof(int),
                         cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess)
-    e = cudaMemsetAsync(b->d_far_count, 0, 2 * sizeof(unsigned), b->stream);
+    e = cudaMemsetAsync(b->d_far_count, 0, 4 * sizeof(unsigned), b->stream);
   // the sources are pageable host memory: each copy is staged before the
   // call returns, so the host tables may be rebuilt right away
   if (e != cudaSuccess) return bfail(b, ELBM_ECUDA, cudaGetErrorString(e));
@@ -388,6 +402,13 @@ static elbm_status reset_stats(elbm_batch* b) {
 
 static cudaError_t run_steps(elbm_batch* b, int nsteps, int diag, int grid) {
   BatchParams bp = batch_params(b);
+  // Both deferred-node counters start every run at zero (within the run,
+  // step s's fixup clears the counter of step s + 1).  Without this the
+  // autotuner's dry steps, which all run as step 0, would never clear
+  // counter 0 and its stale entries would pile up.
+  cudaError_t e0 =
+      cudaMemsetAsync(b->d_far_count, 0, 4 * sizeof(unsigned), b->stream);
+  if (e0 != cudaSuccess) return e0;
   for (int s = 0; s < nsteps; ++s) {
     bp.step = s;
     cudaError_t e = launch_batch(b->tb, diag, bp, grid, b->stream);
@@ -519,6 +540,7 @@ void elbm_batch_destroy(elbm_batch* b) {
   bfree(b, b->d_count, 256);
   bfree(b, b->d_stats, sizeof(MemberStats) * kBatchMaxMembers);
   bfree(b, b->d_far_count, 256);
+  bfree(b, b->d_refine, sizeof(float) * kBatchRefineRows * (size_t)b->refine_cap);
   bfree(b, b->d_err, 256);
   delete b;
 }

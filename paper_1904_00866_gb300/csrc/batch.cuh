@@ -19,7 +19,7 @@
 #pragma once
 #include <stdint.h>
 
-#include "sc32.cuh"
+#include "fixup.cuh"
 
 namespace elbm {
 
@@ -62,7 +62,15 @@ struct BatchParams {
   unsigned* far_count;          // [2]
   unsigned* err_flags;
   int step;                     // step index within the burst
+  // undecided nodes for the second stage: SoA [27 + 3][refine_cap] (the
+  // member's Q stored values, then node and member index as bits and the
+  // provisional alpha);
+  // refine_count[2] indexed like far_count
+  float* refine_buf;
+  unsigned refine_cap;
+  unsigned* refine_count;
 };
+constexpr int kBatchRefineRows = 27 + 3;
 
 __device__ __forceinline__ float* pick(const MemberDesc& m, int parity) {
   return (parity & 1) ? m.buf[1] : m.buf[0];
@@ -207,25 +215,70 @@ __global__ void __launch_bounds__(TB, 2048 / TB / 4)
     const bool stats_step = DIAG && m.diag && bp.step == m.steps_left - 1;
     Acc32 acc;
     if (DIAG) acc.init();
+    unsigned res = kNodeDone;
+    float ap = 0.0f;
     if (node < m.n) {
       float* out = pick(m, m.parity0 + bp.step + 1);
       float* amap = m.alpha_map ? m.alpha_map + node : nullptr;
-      bool ok;
       auto store = [&](int i, float v) { out[(size_t)i * m.n + node] = v; };
       if (m.lattice == 1)
-        ok = sc32_node<D3Q27, true, DIAG, 0, TB>(sm, m.rho0f, m.rho0, m.beta,
-                                                 0.0f, nullptr, amap, acc,
-                                                 store);
+        res = sc32_node<D3Q27, true, DIAG, 0, TB>(sm, m.rho0f, m.rho0, m.beta,
+                                                  0.0f, nullptr, amap, acc,
+                                                  store, &ap);
       else
-        ok = sc32_node<D2Q9, true, DIAG, 0, TB>(sm, m.rho0f, m.rho0, m.beta,
-                                                0.0f, nullptr, amap, acc,
-                                                store);
-      if (!ok) {
-        const unsigned slot = atomicAdd(&bp.far_count[bp.step & 1], 1u);
-        if (slot < bp.far_cap)
-          bp.far_queue[slot] = ((unsigned long long)mi << 32) | node;
-        else
-          atomicOr(bp.err_flags, NF_BAD_NONFINITE);   // cannot happen
+        res = sc32_node<D2Q9, true, DIAG, 0, TB>(sm, m.rho0f, m.rho0, m.beta,
+                                                 0.0f, nullptr, amap, acc,
+                                                 store, &ap);
+    }
+    {
+      // undecided nodes (written provisionally) into the second-stage
+      // buffer, one atomic per warp (every lane gets here: the member is
+      // uniform per block); a full buffer sends them to the tagged queue
+      const unsigned um = __ballot_sync(0xffffffffu, res == kNodeRefine);
+      if (um != 0u) {
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(um) - 1;
+        unsigned base = 0u;
+        if (lane == leader)
+          base = atomicAdd(&bp.refine_count[bp.step & 1],
+                           (unsigned)__popc(um));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (res == kNodeRefine) {
+          const unsigned slot =
+              base + (unsigned)__popc(um & ((1u << lane) - 1u));
+          if (slot < bp.refine_cap) {
+            float* rb = bp.refine_buf + slot;
+            const int q = m.lattice == 1 ? 27 : 9;
+            for (int i = 0; i < q; ++i)
+              rb[(size_t)i * bp.refine_cap] = sm[i * TB];
+            rb[(size_t)27 * bp.refine_cap] = __uint_as_float(node);
+            rb[(size_t)28 * bp.refine_cap] = __uint_as_float((unsigned)mi);
+            rb[(size_t)29 * bp.refine_cap] = ap;
+            res = kNodeDone;
+          }
+        }
+      }
+    }
+    {
+      // deferred nodes, one atomic per warp
+      const unsigned mask = __ballot_sync(0xffffffffu, res != kNodeDone);
+      if (mask != 0u) {
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(mask) - 1;
+        unsigned base = 0u;
+        if (lane == leader)
+          base = atomicAdd(&bp.far_count[bp.step & 1], (unsigned)__popc(mask));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (res != kNodeDone) {
+          const unsigned slot =
+              base + (unsigned)__popc(mask & ((1u << lane) - 1u));
+          if (slot < bp.far_cap)
+            bp.far_queue[slot] =
+                ((unsigned long long)mi << 32) |
+                (node | (res == kNodeRefine ? kTagRefine : 0u));
+          else
+            atomicOr(bp.err_flags, NF_BAD_NONFINITE);   // cannot happen
+        }
       }
     }
     if (DIAG) {
@@ -236,16 +289,32 @@ __global__ void __launch_bounds__(TB, 2048 / TB / 4)
   cp_async_wait<0>();
 }
 
-// FP64 FORMULA for the nodes the batch kernel deferred; clears the other
-// parity's counter for the next step.
+// Deferred nodes of the batch kernel: the double-float second stage for
+// nodes whose FP32 decision was not certified, the FP64 FORMULA for the
+// others and for the still undecided; clears the other parity's counter for
+// the next step.
 template <int DIAG>
 __global__ void __launch_bounds__(256) k_batch_fixup(const BatchParams bp) {
+  const unsigned rcount =
+      bp.refine_cap ? min(bp.refine_count[bp.step & 1], bp.refine_cap) : 0u;
   const unsigned count = min(bp.far_count[bp.step & 1], bp.far_cap);
-  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < count;
+  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < rcount + count;
        k += gridDim.x * blockDim.x) {
-    const unsigned long long e = bp.far_queue[k];
-    const int mi = (int)(e >> 32);
-    const unsigned node = (unsigned)(e & 0xffffffffu);
+    int mi;
+    unsigned tagged;
+    const float* rb = nullptr;   // the node's stored values in the buffer
+    float ap = __int_as_float(0x7fc00000);   // NaN: provisional alpha unknown
+    if (k < rcount) {
+      rb = bp.refine_buf + k;
+      ap = rb[(size_t)29 * bp.refine_cap];
+      tagged = __float_as_uint(rb[(size_t)27 * bp.refine_cap]) | kTagRefine;
+      mi = (int)__float_as_uint(rb[(size_t)28 * bp.refine_cap]);
+    } else {
+      const unsigned long long e = bp.far_queue[k - rcount];
+      mi = (int)(e >> 32);
+      tagged = (unsigned)(e & 0xffffffffu);
+    }
+    const unsigned node = tagged & ~kTagRefine;
     const MemberDesc& m = bp.members[mi];
     const float* in = pick(m, m.parity0 + bp.step);
     float* out = pick(m, m.parity0 + bp.step + 1);
@@ -264,18 +333,29 @@ __global__ void __launch_bounds__(256) k_batch_fixup(const BatchParams bp) {
     pp.err_flags = bp.err_flags;
     pp.secant_iters = 1;
     pp.alpha_map = m.alpha_map;
+    pp.unshifted = 0;
+    pp.corr_rho = 0.0f;
+    bool fp64 = false;
     auto run = [&](auto lat) {
       using L = decltype(lat);
-      Node64<L> nd;
+      float v[L::Q];
 #pragma unroll
       for (int i = 0; i < L::Q; ++i)
-        nd.f[i] = L::w(i) * m.rho0 +
-                  (double)in[(size_t)i * m.n + src_index<L>(g, i, x, y, z)];
-      auto store = [&](int i, double v) {
+        v[i] = rb ? rb[(size_t)i * bp.refine_cap]
+                  : in[(size_t)i * m.n + src_index<L>(g, i, x, y, z)];
+      auto store32 = [&](int i, float val) { out[(size_t)i * m.n + node] = val; };
+      if ((tagged & kTagRefine) &&
+          refine_deferred<L, true, DIAG, 0>(pp, v, node, ap, acc, store32))
+        return;
+      fp64 = true;
+      Node64<L> nd;
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) nd.f[i] = L::w(i) * m.rho0 + (double)v[i];
+      auto store = [&](int i, double val) {
         if (i < 0) {
-          m.alpha_map[node] = (float)v;
+          m.alpha_map[node] = (float)val;
         } else {
-          out[(size_t)i * m.n + node] = (float)(v - L::w(i) * m.rho0);
+          out[(size_t)i * m.n + node] = (float)(val - L::w(i) * m.rho0);
         }
       };
       collide64<L, MODE_FORMULA, 0>(nd, pp, true, acc, DIAG != 0, store);
@@ -293,15 +373,20 @@ __global__ void __launch_bounds__(256) k_batch_fixup(const BatchParams bp) {
       atomicAdd(&st->ke, acc.ke);
       atomicAdd(&st->asum, acc.asum);
       atomicAdd(&st->nodes, 1ull);
-      atomicAdd(&st->far, 1ull);
+      if (fp64) atomicAdd(&st->far, 1ull);
       atomicAdd(&st->acc2, (unsigned long long)acc.acc2);
       atomicAdd(&st->formula, (unsigned long long)acc.formula);
+      atomicAdd(&st->band, (unsigned long long)acc.band);
+      atomicAdd(&st->degen, (unsigned long long)acc.degen);
       const float a = (float)acc.asum;
       atomicMin(&st->amin_bits, __float_as_uint(a));
       atomicMax(&st->amax_bits, __float_as_uint(a));
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) bp.far_count[(bp.step & 1) ^ 1] = 0u;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    bp.far_count[(bp.step & 1) ^ 1] = 0u;
+    if (bp.refine_count) bp.refine_count[(bp.step & 1) ^ 1] = 0u;
+  }
 }
 
 }  // namespace elbm

@@ -1,6 +1,7 @@
 // Launch helpers for the stream-collide kernels; each translation unit
 // instantiates the subset it owns so the kernels compile in parallel.
 #pragma once
+#include "fixup.cuh"
 #include "internal.h"
 #include "sc16.cuh"
 #include "sc32.cuh"

@@ -22,19 +22,24 @@
 // u = 2^-24):  E_x bounds |x_i - x_i exact| (equilibrium products, velocity
 // division, the x division); e2 / e1 bound the errors of Delta H(2) /
 // Delta H(1) from E_x (first and second order), the series rounding and the
-// truncation.  Decision ladder, each rung H-safe for the stored state:
-//   Delta H(2) + e2 <= 0   -> alpha = 2 (acceptance after Eq. (8));
-//   else Delta H(1) + e1 < 0 -> alpha = Eq. (9) chord evaluated on the upper
-//                              bounds and rounded down (the chord root
-//                              decreases in both values, so it stays at or
-//                              below the exact Eq. (9) value, which is at or
-//                              below the root of Eq. (4));
-//   else (node within FP32 noise of equilibrium) -> alpha = 1, for which
-//                              H(f*) = H(f^eq) <= H(f) holds exactly.
-// A node whose n evaluates to exactly zero in FP32 (the degenerate case of
-// the paper seen at FP32 resolution) also takes alpha = 1.
-// When |Delta H(2)| <= e2 the decision is flagged NF_BAND.
-//
+// truncation.  Decision, each branch exact for the stored state:
+//   Delta H(2) + e2 <= 0            -> alpha = 2 (acceptance after Eq. (8));
+//   Delta H(2) - e2 > 0 and Delta H(1) + e1 < 0
+//                                   -> alpha = Eq. (9) chord evaluated on the
+//                                      upper bounds and rounded down (the
+//                                      chord root decreases in both values,
+//                                      so it stays at or below the exact
+//                                      Eq. (9) value, which is at or below
+//                                      the root of Eq. (4));
+//   otherwise (a sign within the FP32 error, or n zero in FP32)
+//                                   -> second stage: n_i recomputed in
+//                                      double-float arithmetic and the same
+//                                      decision retaken with its much smaller
+//                                      error (flag NF_BAND); a node still
+//                                      undecided goes to the FP64 fixup.
+// So every node takes the branch the exact arithmetic takes, except where
+// Delta H(2) lies within the FP64 evaluation's own rounding.
+
 // Opposite-velocity populations are processed in pairs with packed f32x2
 // arithmetic (see npairs below); every lane operation rounds like its
 // scalar form, so only the order of the moment sums differs from a scalar
@@ -42,6 +47,7 @@
 #pragma once
 #include <math.h>
 
+#include "df32.cuh"
 #include "lattice.cuh"
 #include "node_fp64.cuh"
 
@@ -91,6 +97,10 @@ struct N32 {
 __host__ __device__ constexpr int cidx(int c) { return c + 1; }
 
 // 1 / y by the SFU (rcp.approx.ftz.f32, relative error below 2^-23).
+// The other approximate operations below are used with their documented
+// accuracy: rsqrtf within 2 ulp (relative 2^-22), __fdividef within 2 ulp
+// for divisors of normal magnitude.  None of them needs the IEEE
+// division's or square root's special-case path.
 __device__ __forceinline__ float rcp_approx(float y) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y));
@@ -137,6 +147,304 @@ __device__ __forceinline__ void moments2(float v0,
   mx = acc[0].x + acc[0].y;
   my = acc[1].x + acc[1].y;
   mz = L::D == 3 ? acc[2].x + acc[2].y : 0.0f;
+}
+
+// Delta H(2) and Delta H(1) from the moments M[k] = sum_i f_i x_i^k
+// (k = 2..8) by the series sum_k c_k(alpha) M_k,
+// c_k(alpha) = (-1)^k (alpha^k - k alpha) / (k (k-1)), truncated after k = 4
+// (k8 false) or k = 8, with bounds e2 / e1 on their errors given a bound Ex
+// on the absolute error of every x_i: first- and second-order propagation
+// of Ex, rounding of the sums over i and of the series, and the tail.
+struct DH32 {
+  float D2, D1, e2, e1;
+};
+
+template <int Q>
+__device__ __forceinline__ DH32 series_dh32(const float (&M)[9], bool k8,
+                                            float xabs, float Ex, float rho) {
+  constexpr float uu = 5.9604645e-8f;   // 2^-24
+  constexpr float kUp = 1.00000095367431640625f;   // 1 + 2^-20
+  const float gq = (float)(Q + 9) * uu * 1.01f;
+  // c(2): k=3..8: -1/3, 2/3, -11/10, 26/15, -19/7, 30/7
+  // c(1): k=2..8: -1/2, 1/3, -1/4, 1/5, -1/6, 1/7, -1/8
+  DH32 h;
+  h.D2 = fmaf(-1.0f / 3.0f, M[3], (2.0f / 3.0f) * M[4]);
+  h.D1 = fmaf(-0.5f, M[2], fmaf(1.0f / 3.0f, M[3], -0.25f * M[4]));
+  float tr2, tr1, rnd;
+  const float r2 = 2.0f * xabs;
+  if (k8) {
+    h.D2 = fmaf(-1.1f, M[5],
+                fmaf(26.0f / 15.0f, M[6],
+                     fmaf(-19.0f / 7.0f, M[7], fmaf(30.0f / 7.0f, M[8], h.D2))));
+    h.D1 = fmaf(0.2f, M[5],
+                fmaf(-1.0f / 6.0f, M[6],
+                     fmaf(1.0f / 7.0f, M[7], fmaf(-0.125f, M[8], h.D1))));
+    const float r2_7 = r2 * r2 * r2 * r2 * r2 * r2 * r2;
+    const float x7 = xabs * xabs * xabs * xabs * xabs * xabs * xabs;
+    // tails sum_{k>=9}: |c_k(2)| <= 2^k / (k (k-1)), |c_k(1)| = 1 / k,
+    // |M_k| <= xabs^(k-2) M_2; upper bounds of positive quotients are the
+    // 2-ulp approximate division raised by 2^-20
+    tr2 = __fdividef(r2_7, 18.0f * (1.0f - r2)) * kUp;
+    tr1 = __fdividef(x7, 9.0f * (1.0f - xabs)) * kUp;
+    rnd = fabsf(M[5]) * 1.1f + fabsf(M[6]) * 1.74f + fabsf(M[7]) * 2.72f +
+          fabsf(M[8]) * 4.29f;
+  } else {
+    // tails sum_{k>=5}
+    const float r2_3 = r2 * r2 * r2;
+    tr2 = __fdividef(r2_3 * 0.2f, 1.0f - r2) * kUp;
+    tr1 = __fdividef(xabs * xabs * xabs, 5.0f * (1.0f - xabs)) * kUp;
+    rnd = 0.0f;
+  }
+  const float M2 = M[2];
+  h.e2 = M2 * (2.02f * Ex +
+               gq * xabs * (0.34f + xabs * (0.7f + xabs * (1.2f + 1.8f * xabs))) +
+               tr2) +
+         4.0f * uu * (fabsf(M[3]) * (1.0f / 3.0f) + fabsf(M[4]) * (2.0f / 3.0f) +
+                      rnd) +
+         2.0f * rho * (xabs + Ex) * Ex * Ex;
+  // S1b >= sqrt(rho M2) >= sum f |x|  (Cauchy-Schwarz)
+  const float rm = rho * M2;
+  const float S1b = rm > 0.0f ? rm * rsqrtf(rm) * kUp : 0.0f;
+  h.e1 = __fdividef(1.01f * Ex * S1b, 1.0f - xabs) * kUp +
+         M2 * (gq * (0.5f + xabs) + tr1) + 4.0f * uu * (0.5f * M2 + fabsf(M[3])) +
+         2.0f * rho * Ex * Ex;
+  return h;
+}
+
+// The FP32 decision between the acceptance of alpha = 2 (after Eq. (8)) and
+// the chord of Eq. (9), each taken only when certified by the bounds.
+enum { kAcceptTwo = 0, kChord = 1, kUndecided = 2 };
+__device__ __forceinline__ int decide32(const DH32& h, float& alpha) {
+  const float D2hi = __fadd_ru(h.D2, h.e2);
+  if (D2hi <= 0.0f) {
+    alpha = 2.0f;
+    return kAcceptTwo;
+  }
+  const float D1hi = __fadd_ru(h.D1, h.e1);
+  if (!(__fsub_rd(h.D2, h.e2) > 0.0f) || !(D1hi < 0.0f)) return kUndecided;
+  // alpha = 2 + D2hi / (D2hi - D1hi) (1 - 2), rounded down: the chord root
+  // decreases in both values, so it stays at or below the exact Eq. (9)
+  // value.  t = D2hi / (D2hi - D1hi) rounded up: the approximate quotient
+  // (error <= 2 ulp) is raised by 4 ulp
+  const float den = __fsub_rd(D2hi, D1hi);
+  const float tt = __fmul_ru(__fdividef(D2hi, den), 1.0f + 2.384185791e-7f);
+  alpha = __fsub_rd(2.0f, tt);
+  return kChord;
+}
+
+// Mass and momentum sums of the deviations, exact as double-floats.  Each
+// delta = hi + mid + lo with hi on the 2^-20 grid, mid on the 2^-40 grid and
+// |lo| <= 2^-41 (all three splits exact); with sum_i |delta_i| < 4 the hi
+// and mid sums are exact in FP32 (at most 27 terms on their grids) and the
+// lo sum is off by less than 2^-58.  m[0] = sum delta, m[1 + a] = sum c_a
+// delta.
+template <class L>
+__device__ __forceinline__ void exact_moments(float d0,
+                                              const float2 (&dd)[npairs<L>()],
+                                              DF<float> (&m)[4]) {
+  constexpr int P = npairs<L>();
+  constexpr float C20 = 12.0f;                  // 1.5 * 2^3, ulp 2^-20
+  constexpr float C40 = 1.1444091796875e-05f;   // 1.5 * 2^-17, ulp 2^-40
+  float2 h[P], md[P], lw[P];
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    h[k] = sub_(add_(dd[k], f2(C20)), f2(C20));
+    const float2 r1 = sub_(dd[k], h[k]);
+    md[k] = sub_(add_(r1, f2(C40)), f2(C40));
+    lw[k] = sub_(r1, md[k]);
+  }
+  const float h0 = sub_(add_(d0, C20), C20);
+  const float r0 = sub_(d0, h0);
+  const float md0 = sub_(add_(r0, C40), C40);
+  const float lw0 = sub_(r0, md0);
+  float H[4], M[4], W[4];
+  moments2<L>(h0, h, H[0], H[1], H[2], H[3]);
+  moments2<L>(md0, md, M[0], M[1], M[2], M[3]);
+  moments2<L>(lw0, lw, W[0], W[1], W[2], W[3]);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const DF<float> t = two_sum(H[a], M[a]);
+    m[a] = fast_two_sum(t.hi, add_(t.lo, W[a]));
+  }
+}
+
+// Second stage for a node whose FP32 decision is not certified (run by the
+// fixup kernel, out of the stream-collide kernels' register budget): n_i is
+// recomputed in double-float arithmetic from the exact moments, so x_i is
+// known to 6.1 u |x_i| + G (1 + Dd)^3 2^-37 instead of the FP32 path's
+// equilibrium rounding, and the decision is retaken with the bounds of that
+// accuracy (series always to k = 8).  A node still undecided (its Delta H(2)
+// within the double-float error of zero) is deferred to the FP64 fixup
+// (NF_FAR).  Writes r.n0 / r.n2 (the more accurate n, used by the
+// relaxation), r.alpha, r.flags (NF_BAND set: the second stage decided)
+// and the moments r.drho, r.rho, r.j.
+template <class L, bool SHIFTED>
+__device__ __forceinline__ void node32_refine(
+    float d0, const float2 (&dd)[npairs<L>()], float rho0, float corr_rho,
+    const float* __restrict__ corr, float a_extra, N32<L>& r) {
+  constexpr int P = npairs<L>();
+  constexpr float uu = 5.9604645e-8f;  // 2^-24
+  // exact_moments needs sum |delta_i| < 4
+  {
+    float2 sa = make_float2(fabsf(dd[0].x), fabsf(dd[0].y));
+#pragma unroll
+    for (int k = 1; k < P; ++k)
+      sa = add2(sa, make_float2(fabsf(dd[k].x), fabsf(dd[k].y)));
+    if (!(fabsf(d0) + (sa.x + sa.y) < 3.99f)) {
+      r.flags = NF_FAR;
+      return;
+    }
+  }
+  DF<float> m[4];
+  exact_moments<L>(d0, dd, m);
+  DF<float> rho = df_add(m[0], rho0);
+  if (!SHIFTED) rho = df_add(rho, corr_rho);
+  if (!(rho.hi > 0.0f)) {
+    r.flags = NF_FAR;
+    return;
+  }
+  const float rinv = rcp_approx(rho.hi);
+  r.drho = add_(m[0].hi, m[0].lo) + (SHIFTED ? 0.0f : corr_rho);
+  r.rho = rho.hi;
+  r.j[0] = add_(m[1].hi, m[1].lo);
+  r.j[1] = add_(m[2].hi, m[2].lo);
+  r.j[2] = add_(m[3].hi, m[3].lo);
+
+  // per-axis factors psi[a][c + 1] = 1 + d_a(c) of the entropic equilibrium
+  DF<float> psi[3][3];
+  float U = 0.0f;
+#pragma unroll
+  for (int a = 0; a < L::D; ++a) {
+    // u = j / rho: FP32 quotient plus the corrected residual
+    const DF<float> j = m[a + 1];
+    const float q = mul_(j.hi, rinv);
+    const DF<float> qp = two_prod(q, rho.hi);
+    const float res = sub_(add_(sub_(sub_(j.hi, qp.hi), qp.lo), j.lo),
+                           mul_(q, rho.lo));
+    const DF<float> u = fast_two_sum(q, mul_(res, rinv));
+    U = fmaxf(U, fabsf(u.hi));
+    // s = sqrt(1 + 3u^2) - 1: one Newton step on s^2 + 2s - 3u^2 = 0 from
+    // the FP32 value (relative error 9.5 u, squared by the step)
+    const float y = fmaf(3.0f * u.hi, u.hi, 1.0f);
+    const float s0 = 3.0f * u.hi * u.hi * rcp_approx(1.0f + y * rsqrtf(y));
+    const DF<float> sq = two_prod(s0, s0);
+    const DF<float> t = two_sum(sq.hi, add_(s0, s0));
+    const DF<float> u3 = df_mul(u, 3.0f);
+    const DF<float> u23 = df_mul(u3, u);
+    const float g =
+        add_(sub_(t.hi, u23.hi), sub_(add_(t.lo, sq.lo), u23.lo));
+    const DF<float> sv =
+        fast_two_sum(s0, mul_(neg_(g), rcp_approx(fma_(2.0f, s0, 2.0f))));
+    const DF<float> s2 = {add_(sv.hi, sv.hi), add_(sv.lo, sv.lo)};
+    psi[a][2] = df_add(df_add(u3, s2), 1.0f);           // 1 + 3u + 2s
+    psi[a][0] = df_add(df_add(df_neg(u3), s2), 1.0f);   // 1 - 3u + 2s
+    psi[a][1] = df_add(df_neg(sv), 1.0f);               // 1 - s
+  }
+  if (!(U < 0.5f)) {
+    r.flags = NF_FAR;
+    return;
+  }
+  // n_i = W_i (rho P_i - rho0) [+ corr_i] - delta_i, P_i = prod_a psi_a;
+  // W_i as double-float constants per weight class (compile-time tables)
+  constexpr float whi[4] = {df_hi(L::w(0)), df_hi(L::w(1)),
+                            df_hi(L::w(L::D == 3 ? 7 : 5)),
+                            df_hi(L::w(L::D == 3 ? 19 : 5))};
+  constexpr float wlo[4] = {df_lo(L::w(0)), df_lo(L::w(1)),
+                            df_lo(L::w(L::D == 3 ? 7 : 5)),
+                            df_lo(L::w(L::D == 3 ? 19 : 5))};
+  auto wdf = [&](int i) {
+    return DF<float>{whi[wclass<L>(i)], wlo[wclass<L>(i)]};
+  };
+  float w0[4];
+#pragma unroll
+  for (int k = 0; k <= L::D; ++k)
+    w0[k] = (k == 0 ? L::wf(0) : L::wf(k == 1 ? 1 : (k == 2 ? 7 : 19))) * rho0;
+  float M[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  float xabs;
+  {
+    DF<float> Pr = df_mul(psi[0][1], psi[1][1]);
+    if (L::D == 3) Pr = df_mul(Pr, psi[2][1]);
+    DF<float> t = df_mul(df_add(df_mul(rho, Pr), -rho0), wdf(0));
+    if (!SHIFTED) t = df_add(t, corr[0]);
+    t = df_add(t, -d0);
+    const float ni = add_(t.hi, t.lo);
+    r.n0 = ni;
+    const float x = ni * rcp_approx(w0[0] + d0);
+    xabs = fabsf(x);
+    float pw = ni * x;   // n x^(k-1) = f x^k
+#pragma unroll
+    for (int k = 2; k <= 8; ++k) {
+      M[k] = pw;
+      pw *= x;
+    }
+  }
+  auto pair = [&](int a, int c) { return df_pair(psi[a][c + 1], psi[a][1 - c]); };
+  DF<float2> pxy[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) pxy[a][b] = df_mul(pair(0, a - 1), pair(1, b - 1));
+  float2 mk[9];
+#pragma unroll
+  for (int k = 2; k <= 8; ++k) mk[k] = f2(0.0f);
+  const DF<float2> rho2 = df_bcast(rho);
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    const int i = 2 * k + 1;
+    DF<float2> Pp = pxy[cidx(L::c(i, 0))][cidx(L::c(i, 1))];
+    if (L::D == 3) Pp = df_mul(Pp, pair(2, L::c(i, 2)));
+    DF<float2> t = df_add(df_mul(rho2, Pp), f2(-rho0));
+    t = df_mul(t, df_bcast(wdf(i)));
+    if (!SHIFTED) t = df_add(t, make_float2(corr[i], corr[i + 1]));
+    t = df_add(t, neg_(dd[k]));
+    const float2 ni = add_(t.hi, t.lo);
+    r.n2[k] = ni;
+    const int kc = wclass<L>(i);
+    const float2 x = mul2(ni, rcp_approx2(add2(f2(w0[kc]), dd[k])));
+    xabs = fmaxf(xabs, fmaxf(fabsf(x.x), fabsf(x.y)));
+    float2 pw = mul2(ni, x);
+#pragma unroll
+    for (int e = 2; e <= 8; ++e) {
+      mk[e] = add2(mk[e], pw);
+      pw = mul2(pw, x);
+    }
+  }
+#pragma unroll
+  for (int k = 2; k <= 8; ++k) M[k] += mk[k].x + mk[k].y;
+  if (!(xabs <= 0.125f)) {
+    r.flags = NF_FAR;
+    return;
+  }
+  if (xabs == 0.0f) {
+    // n == 0 to double-float accuracy: alpha = 1 (f* = f^eq) keeps
+    // H(f*) <= H(f) exactly; the relaxation leaves f unchanged either way
+    r.flags = NF_DEGENERATE | NF_BAND;
+    r.alpha = 1.0f;
+    return;
+  }
+  // Error of x_i: the rounding of n_i to FP32, of f_i and of the quotient
+  // (6.1 u |x_i|) plus the double-float error of n_i, at most
+  // W_i rho (1 + Dd)^3 2^-37 (per-axis factors within 2^-40, products and
+  // the final sums within 8 u^2 of their magnitudes), divided by
+  // f_i >= W_i rho / G.
+  constexpr float kUp = 1.00000095367431640625f;   // 1 + 2^-20
+  const float Dd = fmaf(3.0f * U, U, 3.0f * U);
+  const float omd = 1.0f - Dd;
+  const float omdD = L::D == 3 ? omd * omd * omd : omd * omd;
+  const float G = __fdividef(1.0f + xabs, omdD) * kUp;
+  const float opd3 = (1.0f + Dd) * (1.0f + Dd) * (1.0f + Dd);
+  const float Ex = 1.01f * (6.1f * uu * xabs +
+                            G * (opd3 * 7.275957614183426e-12f + a_extra));
+  const DH32 h = series_dh32<L::Q>(M, true, xabs, Ex, rho.hi);
+  float alpha = 1.0f;
+  const int k = decide32(h, alpha);
+  if (k == kUndecided) {
+    r.flags = NF_FAR;
+    return;
+  }
+  r.alpha = alpha;
+  r.flags = NF_BAND | (k == kAcceptTwo ? (NF_ACCEPT_TWO | NF_ACCEPT_STAR)
+                                       : NF_FORMULA);
 }
 
 // d0, dd: FP32 deviations delta_i of the rest population and the pairs
@@ -186,7 +494,11 @@ __device__ __forceinline__ void node32_formula(
   for (int a = 0; a < L::D; ++a) {
     const float u = j[a] * inv_rho;
     U = fmaxf(U, fabsf(u));
-    const float s = 3.0f * u * u / (1.0f + sqrtf(fmaf(3.0f * u, u, 1.0f)));
+    // s = 3u^2 / (1 + sqrt(1 + 3u^2)), relative error <= 9.5 u (numerator
+    // 2 u, 1 + 3u^2 2 u, its root via rsqrtf 6 u, 1 + root 4.5 u, the
+    // reciprocal 2 u, the product u)
+    const float y = fmaf(3.0f * u, u, 1.0f);
+    const float s = 3.0f * u * u * rcp_approx(1.0f + y * rsqrtf(y));
     dp[a] = fmaf(3.0f, u, 2.0f * s);
     dm[a] = fmaf(-3.0f, u, 2.0f * s);
     dz[a] = -s;
@@ -275,28 +587,27 @@ __device__ __forceinline__ void node32_formula(
   }
   if (xabs == 0.0f) {
     // f^eq == f in FP32 only: the exact state may still differ from its
-    // equilibrium below FP32 resolution, where alpha = 2 can raise H by a
-    // rounding-level amount.  alpha = 1 (f* = f^eq) keeps H(f*) <= H(f)
-    // exactly; the relaxation writes f unchanged either way (n = 0).
-    r.flags = NF_DEGENERATE;
+    // equilibrium below FP32 resolution; the second stage decides (the
+    // provisional alpha is immaterial: n = 0 leaves f unchanged)
+    r.flags = NF_REFINE;
     r.alpha = 1.0f;
     return;
   }
   // longer series for nodes further from equilibrium
   const bool k8 = xabs > 0.01f;
-  float M5 = 0.f, M6 = 0.f, M7 = 0.f, M8 = 0.f;
+  float M[9] = {0.f, 0.f, M2, M3, M4, 0.f, 0.f, 0.f, 0.f};
   if (k8) {
     {
       const float x = r.n0 * rcp_approx(w0[0] + d0);
       const float x2 = x * x;
       float p = r.n0 * x2 * x2;   // n x^4 = f x^5
-      M5 = p;
+      M[5] = p;
       p *= x;
-      M6 = p;
+      M[6] = p;
       p *= x;
-      M7 = p;
+      M[7] = p;
       p *= x;
-      M8 = p;
+      M[8] = p;
     }
     float2 m5 = f2(0.0f), m6 = f2(0.0f), m7 = f2(0.0f), m8 = f2(0.0f);
 #pragma unroll
@@ -313,89 +624,46 @@ __device__ __forceinline__ void node32_formula(
       p = mul2(p, x);
       m8 = add2(m8, p);
     }
-    M5 += m5.x + m5.y;
-    M6 += m6.x + m6.y;
-    M7 += m7.x + m7.y;
-    M8 += m8.x + m8.y;
+    M[5] += m5.x + m5.y;
+    M[6] += m6.x + m6.y;
+    M[7] += m7.x + m7.y;
+    M[8] += m8.x + m8.y;
   }
 
   // ---- error bounds -------------------------------------------------------
   const float Dd = fmaf(3.0f * U, U, 3.0f * U);      // max |d_a|
   const float Eu = 4.0f * uu * U + 2e-11f * inv_rho;
-  const float Ed = (3.0f + 6.0f * U) * Eu + 6.0f * uu * U * (1.0f + 2.5f * U);
+  // |d(d)/du| <= 3 + 6U; rounding of d = fma(+-3, u, 2s): u (3U + 3U^2),
+  // of 2s: 19 u s <= 28.5 u U^2
+  const float Ed = (3.0f + 6.0f * U) * Eu + 6.0f * uu * U * (1.0f + 5.5f * U);
   const float opd2 = (1.0f + Dd) * (1.0f + Dd);
   const float EP = (3.0f * Ed + 18.0f * uu * Dd) * opd2;
   const float omd = 1.0f - Dd;
   const float omdD = L::D == 3 ? omd * omd * omd : omd * omd;
-  const float G = (1.0f + xabs) / omdD;
+  // upper bound of a positive quotient: the 2-ulp approximate division
+  // raised by 2^-20 (covers its error and the product's rounding)
+  constexpr float kUp = 1.00000095367431640625f;   // 1 + 2^-20
+  const float G = __fdividef(1.0f + xabs, omdD) * kUp;
   const float Ex =
       1.05f * (G * (EP + 3.0f * uu * (fabsf(drho) * inv_rho + 3.0f * Dd) +
                     2e-11f * inv_rho + a_extra) +
                6.0f * uu * xabs);
-  const float gq = (float)(Q + 9) * uu * 1.01f;
-
-  // c_k(alpha) = (-1)^k (alpha^k - k alpha) / (k (k-1))
-  // c(2): k=3..8: -1/3, 2/3, -11/10, 26/15, -19/7, 30/7
-  // c(1): k=2..8: -1/2, 1/3, -1/4, 1/5, -1/6, 1/7, -1/8
-  float D2 = fmaf(-1.0f / 3.0f, M3, (2.0f / 3.0f) * M4);
-  float D1 = fmaf(-0.5f, M2, fmaf(1.0f / 3.0f, M3, -0.25f * M4));
-  float tr2, tr1, rnd;
-  const float r2 = 2.0f * xabs;
-  if (k8) {
-    D2 = fmaf(-1.1f, M5, fmaf(26.0f / 15.0f, M6, fmaf(-19.0f / 7.0f, M7,
-                                                  fmaf(30.0f / 7.0f, M8, D2))));
-    D1 = fmaf(0.2f, M5, fmaf(-1.0f / 6.0f, M6,
-                             fmaf(1.0f / 7.0f, M7, fmaf(-0.125f, M8, D1))));
-    const float r2_7 = r2 * r2 * r2 * r2 * r2 * r2 * r2;
-    const float x7 = xabs * xabs * xabs * xabs * xabs * xabs * xabs;
-    // tails sum_{k>=9}: |c_k(2)| <= 2^k / (k (k-1)), |c_k(1)| = 1 / k,
-    // |M_k| <= xabs^(k-2) M_2
-    tr2 = r2_7 / (18.0f * (1.0f - r2));
-    tr1 = x7 / (9.0f * (1.0f - xabs));
-    rnd = fabsf(M5) * 1.1f + fabsf(M6) * 1.74f + fabsf(M7) * 2.72f +
-          fabsf(M8) * 4.29f;
-  } else {
-    // tails sum_{k>=5}
-    const float r2_3 = r2 * r2 * r2;
-    tr2 = r2_3 * 0.2f / (1.0f - r2);
-    tr1 = xabs * xabs * xabs / (5.0f * (1.0f - xabs));
-    rnd = 0.0f;
-  }
-  const float e2 =
-      M2 * (2.02f * Ex +
-            gq * xabs * (0.34f + xabs * (0.7f + xabs * (1.2f + 1.8f * xabs))) +
-            tr2) +
-      4.0f * uu * (fabsf(M3) * (1.0f / 3.0f) + fabsf(M4) * (2.0f / 3.0f) + rnd) +
-      2.0f * rho * (xabs + Ex) * Ex * Ex;
-  const float S1b = sqrtf(rho * M2);   // >= sum f |x|  (Cauchy-Schwarz)
-  const float e1 = 1.01f * Ex * S1b / (1.0f - xabs) +
-                   M2 * (gq * (0.5f + xabs) + tr1) +
-                   4.0f * uu * (0.5f * M2 + fabsf(M3)) + 2.0f * rho * Ex * Ex;
-
-  const float D2hi = __fadd_ru(D2, e2);
-  if (D2hi <= 0.0f) {
-    r.flags = NF_ACCEPT_TWO | NF_ACCEPT_STAR;
-    r.alpha = 2.0f;
+  const DH32 h = series_dh32<Q>(M, k8, xabs, Ex, rho);
+  float alpha = 2.0f;
+  const int k = decide32(h, alpha);
+  if (k == kUndecided) {
+    // the sign of Delta H(2) or of Delta H(1) is within the FP32 error:
+    // the second stage (node32_refine) decides.  The provisional alpha
+    // follows the nominal FP32 values; the populations written with it
+    // are replaced where the decided alpha changes them.
+    r.flags = NF_REFINE;
+    r.alpha = h.D2 <= 0.0f
+                  ? 2.0f
+                  : (h.D1 < 0.0f ? 2.0f - __fdividef(h.D2, h.D2 - h.D1) : 1.0f);
     return;
   }
-  const float D1hi = __fadd_ru(D1, e1);
-  if (!(D1hi < 0.0f)) {
-    // Within FP32 noise of equilibrium: neither sign is certified, but
-    // alpha = 1 (f* = f^eq) satisfies H(f*) <= H(f) exactly.  Here n is at
-    // the level of the FP32 error of the equilibrium, so the relaxation
-    // rate it implies is immaterial.
-    r.flags = NF_FORMULA | NF_BAND;
-    r.alpha = 1.0f;
-    return;
-  }
-  const bool band = __fsub_rd(D2, e2) <= 0.0f;
-  // alpha = 2 + D2hi / (D2hi - D1hi) (1 - 2), rounded down
-  // t = D2hi / (D2hi - D1hi) rounded up: the approximate quotient (error
-  // <= 2 ulp) is raised by 4 ulp
-  const float den = __fsub_rd(D2hi, D1hi);
-  const float tt = __fmul_ru(__fdividef(D2hi, den), 1.0f + 2.384185791e-7f);
-  r.alpha = __fsub_rd(2.0f, tt);
-  r.flags = NF_FORMULA | (band ? NF_BAND : 0u);
+  r.alpha = alpha;
+  r.flags = k == kAcceptTwo ? (NF_ACCEPT_TWO | NF_ACCEPT_STAR) : NF_FORMULA;
 }
 
 // Conservation projection of n (applied to the relaxation only): removes

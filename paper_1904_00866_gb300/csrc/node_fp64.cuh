@@ -33,7 +33,8 @@ enum : unsigned {
   NF_NO_ROOT = 128u,
   NF_BAD_NEG = 256u,
   NF_BAD_NONFINITE = 512u,
-  NF_TIMEOUT = 1024u     // a bounded pipeline wait ran out (kernel left)
+  NF_TIMEOUT = 1024u,    // a bounded pipeline wait ran out (kernel left)
+  NF_REFINE = 2048u      // FP32 decision not certified: second stage due
 };
 
 enum { MODE_FORMULA = 0, MODE_ROOT = 1, MODE_SECANT = 2 };

@@ -2,9 +2,12 @@
 // handle and buffer management, initialisation / readout kernels, the
 // per-step launch sequence and the diagnostics finish kernel.
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <string>
 #include <vector>
@@ -128,8 +131,10 @@ struct elbm_handle {
   double* stats_dev = nullptr;
   double* fields = nullptr;   // (1 + D) x n doubles: rho, u staging
   unsigned* err_flags = nullptr;
-  unsigned* far_count = nullptr;
+  unsigned* far_count = nullptr;   // [0..1] deferred, [2..3] undecided
   unsigned* far_queue = nullptr;
+  float* refine_buf = nullptr;     // undecided-node buffer [q + 2][cap]
+  unsigned refine_cap = 0;
   long long step = 0;
   int diag_every = 1, check_every = 0, amap_every = 0, secant_iters = 4;
   bool stats_valid = false;
@@ -219,8 +224,17 @@ static elbm_status ensure_buffers(elbm_handle* h) {
   h->stats_dev = (double*)dev_alloc(h, sizeof(double) * NSTAT);
   h->err_flags = (unsigned*)dev_alloc(h, 256);
   h->far_count = (unsigned*)dev_alloc(h, 256);
-  if (h->dtype != ELBM_FP64)
+  if (h->dtype != ELBM_FP64) {
     h->far_queue = (unsigned*)dev_alloc(h, sizeof(unsigned) * h->n);
+    // Undecided nodes of a step (about 1-3 % on developed flows; nearly all
+    // on the first step after initialisation, where the overflow takes the
+    // gather path): n / 16 entries, at least 65,536.
+    const long long cap =
+        std::min<long long>(h->n, std::max<long long>(h->n / 16, 65536));
+    h->refine_buf = (float*)dev_alloc(
+        h, sizeof(float) * (size_t)(h->q + 2) * (size_t)cap);
+    h->refine_cap = h->refine_buf ? (unsigned)cap : 0u;
+  }
   if (!h->f[0] || !h->f[1] || !h->partials || !h->stats_dev ||
       !h->err_flags || !h->far_count ||
       (h->dtype != ELBM_FP64 && !h->far_queue))
@@ -333,6 +347,10 @@ elbm_status elbm_create(elbm_handle** out, elbm_lattice lattice, int nx,
   const int q = lattice == ELBM_D1Q3 ? 3 : (lattice == ELBM_D2Q9 ? 9 : 27);
   if (n > 0xffffffffLL || (long long)q * n > (1LL << 40))
     return fail(nullptr, ELBM_EINVAL, "lattice too large");
+  // the deferred-node queue of FP32 / FP16 storage tags entries in bit 31
+  if (dtype != ELBM_FP64 && n >= (1LL << 31))
+    return fail(nullptr, ELBM_EINVAL,
+                "FP32 / FP16 storage supports fewer than 2^31 nodes");
   elbm_handle* h = new elbm_handle();
   h->lattice = lattice;
   h->nx = nx;
@@ -545,9 +563,12 @@ elbm_status elbm_step(elbm_handle* h, long long nsteps, elbm_alpha_mode mode) {
   p.far_count = h->far_count;
   p.far_queue = h->far_queue;
   p.far_cap = h->far_queue ? (unsigned)h->n : 0u;
+  p.refine_buf = h->refine_buf;
+  p.refine_cap = h->refine_cap;
+  p.refine_count = h->far_count + 2;
   // the deferred-node counters start every call at zero; within the call
   // each step's fixup clears the counter the next step uses
-  if (nsteps > 0) cudaMemsetAsync(h->far_count, 0, 2 * sizeof(unsigned),
+  if (nsteps > 0) cudaMemsetAsync(h->far_count, 0, 4 * sizeof(unsigned),
                                   h->stream);
   const bool d2 = h->lattice == ELBM_D2Q9;
   // 0: FP64, 1: FP32 (shifted or not), 2: FP16-shifted
@@ -612,7 +633,9 @@ elbm_status elbm_step(elbm_handle* h, long long nsteps, elbm_alpha_mode mode) {
     if (fp32_formula) {
       StepParams pf = p;
       pf.partials = h->partials + (size_t)grid * NSTAT;
-      const int fgrid = grid < 152 ? grid : 152;
+      // as many blocks as the step: the second stage of undecided nodes
+      // runs here too, and its gathers want the parallelism
+      const int fgrid = grid;
       if (storage == 2)
         e = d2 ? launch_far16_d2q9(diag, check, pf, fgrid, h->stream)
                : launch_far16_d3q27(diag, check, pf, fgrid, h->stream);
@@ -734,6 +757,10 @@ elbm_status elbm_entropy_stats(elbm_handle* h, elbm_entropy_stats_t* out) {
   if (e != cudaSuccess) return cuda_fail(h, e, "copy stats");
   stats_from_slots(s, h->dtype == ELBM_FP64 ? 0.0 : h->rho0, h->n,
                    h->stats_step, h->stats_checked, out);
+  if (out->n_root_cap > 0)
+    return fail(h, ELBM_EROOT_CAP,
+                std::to_string(out->n_root_cap) +
+                    " node(s) stopped ROOT bisection at the iteration cap");
   return ELBM_OK;
 }
 
@@ -776,6 +803,8 @@ size_t elbm_device_bytes(const elbm_handle* h) { return h ? h->bytes : 0; }
 long long elbm_launch_count(void) { return g_launches.load(); }
 
 double elbm_rho0(const elbm_handle* h) { return h ? h->rho0 : 0.0; }
+
+double elbm_beta(const elbm_handle* h) { return h ? h->beta : NAN; }
 
 elbm_status elbm_set_profiling(elbm_handle* h, int enable) {
   if (!h) return ELBM_EINVAL;

@@ -73,26 +73,26 @@ __global__ void __launch_bounds__(kSc32Threads, 2)
     const unsigned upper = upper_cur;
     upper_cur = upper_next;
     stage ^= 1;
-    if (node >= (unsigned)p.n) continue;
-    const bool done = sc32_node_in<L, true, DIAG, CHECK>(
-        [&](int i) {
-          const unsigned w = sm[i * kSc32Threads];
-          const unsigned sh = ((upper >> i) & 1u) << 4;
-          return h16_dev<L>((unsigned short)(w >> sh), i);
-        },
-        rho0f, p.rho0, beta, 0.0f, nullptr,
-        p.alpha_map ? p.alpha_map + node : nullptr, acc,
-        [&](int i, float v) {
-          reinterpret_cast<unsigned short*>(p.out_pop[i])[node] =
-              h16_bits<L>(v, i);
-        });
-    if (!done) {
-      const unsigned slot = atomicAdd(&p.far_count[p.parity], 1u);
-      if (slot < p.far_cap)
-        p.far_queue[slot] = node;
-      else
-        atomicOr(p.err_flags, NF_BAD_NONFINITE);   // cannot happen: cap = n
-    }
+    // stored values: the decoded deviations
+    auto in = [&](int i) {
+      const unsigned w = sm[i * kSc32Threads];
+      const unsigned sh = ((upper >> i) & 1u) << 4;
+      return h16_dev<L>((unsigned short)(w >> sh), i);
+    };
+    unsigned st = kNodeDone;
+    float ap = 0.0f;
+    if (node < (unsigned)p.n)
+      st = sc32_node_in<L, true, DIAG, CHECK>(
+          in, rho0f, p.rho0, beta, 0.0f, nullptr,
+          p.alpha_map ? p.alpha_map + node : nullptr, acc,
+          [&](int i, float v) {
+            reinterpret_cast<unsigned short*>(p.out_pop[i])[node] =
+                h16_bits<L>(v, i);
+          },
+          &ap);
+    defer_undecided<L>(p, st == kNodeRefine, in, node, ap);
+    defer_nodes(&p.far_count[p.parity], p.far_queue, p.far_cap, p.err_flags,
+                node, st == kNodeFar ? kNodeFar : kNodeDone);
   }
   cp_async_wait<0>();
   if (DIAG) store_acc32(acc, p.partials);

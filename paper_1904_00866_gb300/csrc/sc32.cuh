@@ -124,20 +124,26 @@ __device__ __forceinline__ void issue_tile(const StepParams& p, float* sm,
   }
 }
 
-// Collision of one node whose Q gathered values are returned by in(i)
-// (shared memory).  Writes the Q post-collision values through
-// out(i, value) and the alpha through amap (nullable).  Returns false when
-// the node must go to the FP64 fixup (nothing written).
-template <class L, bool SHIFTED, int DIAG, int CHECK, class In, class Out>
-__device__ __forceinline__ bool sc32_node_in(In in, float rho0f, double rho0,
-                                             float beta, float corr_rho,
-                                             const float* __restrict__ corr,
-                                             float* amap, Acc32& acc,
-                                             Out out) {
-  constexpr int Q = L::Q;
+// Outcome of the FP32 stage of one node in the stream-collide kernels.
+enum : unsigned {
+  kNodeDone = 0u,     // collided and stored
+  kNodeFar = 1u,      // far from equilibrium or invalid: FP64 fixup
+  kNodeRefine = 2u    // FP32 decision not certified: second stage in the
+                      // fixup kernel (double-float, FP64 as a last resort)
+};
+// Deferred-node queue entries carry the node index; this bit marks the
+// entries due for the second stage.  Node indices stay below 2^31.
+constexpr unsigned kTagRefine = 0x80000000u;
+
+// Deviations delta_i of a node from its stored values in(i): the values
+// themselves for shifted storage, v_i - fl(W_i rho0) for plain FP32
+// storage (exact unless v_i leaves [s_i / 2, 2 s_i]; a_extra bounds the
+// resulting error of x_i).
+template <class L, bool SHIFTED, class In>
+__device__ __forceinline__ void load_deviations(In in, float rho0f, float& d0,
+                                                float2 (&dd)[npairs<L>()],
+                                                float& a_extra) {
   constexpr int P = npairs<L>();
-  float d0;
-  float2 dd[P];
   {
     const float v = in(0);
     d0 = SHIFTED ? v : v - L::wf(0) * rho0f;
@@ -147,18 +153,22 @@ __device__ __forceinline__ bool sc32_node_in(In in, float rho0f, double rho0,
     const float2 v = make_float2(in(2 * k + 1), in(2 * k + 2));
     dd[k] = SHIFTED ? v : sub2(v, f2(L::wf(2 * k + 1) * rho0f));
   }
-  float a_extra = 0.0f;
+  a_extra = 0.0f;
   if (!SHIFTED) {
-    // delta_i = v_i - s_i is exact unless v_i leaves [s_i/2, 2 s_i]
     float A = fabsf(d0);
 #pragma unroll
     for (int k = 0; k < P; ++k) A += fabsf(dd[k].x) + fabsf(dd[k].y);
     a_extra = 2.0f * 5.9604645e-8f * A / rho0f;
   }
-  N32<L> r;
-  node32_formula<L, SHIFTED>(d0, dd, rho0f, corr_rho, corr, a_extra, r);
-  if (r.flags & NF_FAR) return false;
-  // relax with the conservation-projected n:  f~ = f + alpha beta n
+}
+
+// Relaxation with the conservation-projected n, f~ = f + alpha beta n
+// (Eq. (1)), stored through out(i, value) as the storage's value.
+template <class L, bool SHIFTED, class Out>
+__device__ __forceinline__ void relax_store32(const N32<L>& r, float d0,
+                                              const float2 (&dd)[npairs<L>()],
+                                              float rho0f, float beta,
+                                              Out out) {
   const float ab = r.alpha * beta;
   projection<L>(
       r,
@@ -172,50 +182,232 @@ __device__ __forceinline__ bool sc32_node_in(In in, float rho0f, double rho0,
         out(2 * k + 1, nv.x);
         out(2 * k + 2, nv.y);
       });
-  if (amap) *amap = r.alpha;
-  if (DIAG) {
-    acc.nodes += 1;
-    acc.drho.add(r.drho);
-    acc.j0.add(r.j[0]);
-    acc.j1.add(r.j[1]);
-    acc.j2.add(r.j[2]);
-    acc.ke.add(0.5f * (r.j[0] * r.j[0] + r.j[1] * r.j[1] + r.j[2] * r.j[2]) /
-               r.rho);
-    acc.asum.add(r.alpha);
-    acc.amin = fminf(acc.amin, r.alpha);
-    acc.amax = fmaxf(acc.amax, r.alpha);
-    acc.acc2 += (r.flags & NF_ACCEPT_TWO) != 0;
-    acc.formula += (r.flags & NF_FORMULA) != 0;
-    acc.band += (r.flags & NF_BAND) != 0;
-    acc.degen += (r.flags & NF_DEGENERATE) != 0;
-    if (CHECK) {
-      Node64<L> nd;
+}
+
+// The second stage's correction of a node written with the provisional
+// alpha ap: the populations relaxed with the decided alpha ae (same n, same
+// operations), stored through out(i, value) only where they differ from
+// the provisional ones (most differ by less than the storage rounding).
+template <class L, bool SHIFTED, class Out>
+__device__ __forceinline__ void relax_update32(const N32<L>& r, float ap,
+                                               float ae, float d0,
+                                               const float2 (&dd)[npairs<L>()],
+                                               float rho0f, float beta,
+                                               Out out) {
+  const float abp = ap * beta, abe = ae * beta;
+  projection<L>(
+      r,
+      [&](float wt) {
+        const float m = r.n0 - wt;
+        float vp = fmaf(abp, m, d0), ve = fmaf(abe, m, d0);
+        if (!SHIFTED) {
+          vp += L::wf(0) * rho0f;
+          ve += L::wf(0) * rho0f;
+        }
+        if (ve != vp) out(0, ve);
+      },
+      [&](int k, float2 wt) {
+        const float2 m = sub2(r.n2[k], wt);
+        float2 vp = fma2(f2(abp), m, dd[k]), ve = fma2(f2(abe), m, dd[k]);
+        if (!SHIFTED) {
+          vp = add2(vp, f2(L::wf(2 * k + 1) * rho0f));
+          ve = add2(ve, f2(L::wf(2 * k + 1) * rho0f));
+        }
+        if (ve.x != vp.x) out(2 * k + 1, ve.x);
+        if (ve.y != vp.y) out(2 * k + 2, ve.y);
+      });
+}
+
+// FP64 entropy check (Eq. (7)) of a node given its stored values in(i), at
+// the alpha used.
+template <class L, bool SHIFTED, class In>
+__device__ __forceinline__ Check64 check32(In in, double rho0, float alpha,
+                                           Node64<L>& nd) {
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const double v = (double)in(i);
-        nd.f[i] = SHIFTED ? L::w(i) * rho0 + v : v;
-      }
-      node64_prepare(nd);
-      Check64 ck = node64_check(nd, (double)r.alpha);
-      acc.h += ck.h;
-      acc.viol += ck.violation;
-      acc.mismatch += ((r.flags & NF_ACCEPT_STAR) != 0) != ck.accept_ref;
-      acc.adev = fmax(acc.adev, fabs((double)r.alpha - ck.alpha_ref));
-    }
+  for (int i = 0; i < L::Q; ++i) {
+    const double v = (double)in(i);
+    nd.f[i] = SHIFTED ? L::w(i) * rho0 + v : v;
   }
+  node64_prepare(nd);
+  return node64_check(nd, (double)alpha);
+}
+
+// Statistics of one collided node (FP32 accumulators).
+template <class L, bool SHIFTED, int CHECK, class In>
+__device__ __forceinline__ void diag32(const N32<L>& r, In in, double rho0,
+                                       Acc32& acc) {
+  acc.nodes += 1;
+  acc.drho.add(r.drho);
+  acc.j0.add(r.j[0]);
+  acc.j1.add(r.j[1]);
+  acc.j2.add(r.j[2]);
+  acc.ke.add(0.5f * (r.j[0] * r.j[0] + r.j[1] * r.j[1] + r.j[2] * r.j[2]) /
+             r.rho);
+  acc.asum.add(r.alpha);
+  acc.amin = fminf(acc.amin, r.alpha);
+  acc.amax = fmaxf(acc.amax, r.alpha);
+  acc.acc2 += (r.flags & NF_ACCEPT_TWO) != 0;
+  acc.formula += (r.flags & NF_FORMULA) != 0;
+  acc.band += (r.flags & NF_BAND) != 0;
+  acc.degen += (r.flags & NF_DEGENERATE) != 0;
+  if (CHECK) {
+    Node64<L> nd;
+    const Check64 ck = check32<L, SHIFTED>(in, rho0, r.alpha, nd);
+    acc.h += ck.h;
+    acc.viol += ck.violation;
+    acc.mismatch += ((r.flags & NF_ACCEPT_STAR) != 0) != ck.accept_ref;
+    acc.adev = fmax(acc.adev, fabs((double)r.alpha - ck.alpha_ref));
+  }
+}
+
+// Collision of one node whose Q gathered values are returned by in(i)
+// (shared memory).  Writes the Q post-collision values through
+// out(i, value) and the alpha through amap (nullable).  Returns kNodeDone;
+// kNodeRefine for a node whose FP32 decision is undecided (populations
+// written with the provisional alpha, no statistics or alpha map: the
+// second stage completes it); or kNodeFar (nothing written: the FP64 fixup
+// collides it).
+template <class L, bool SHIFTED, int DIAG, int CHECK, class In, class Out>
+__device__ __forceinline__ unsigned sc32_node_in(
+    In in, float rho0f, double rho0, float beta, float corr_rho,
+    const float* __restrict__ corr, float* amap, Acc32& acc, Out out,
+    float* aprov = nullptr) {
+  constexpr int P = npairs<L>();
+  float d0, a_extra;
+  float2 dd[P];
+  load_deviations<L, SHIFTED>(in, rho0f, d0, dd, a_extra);
+  N32<L> r;
+  node32_formula<L, SHIFTED>(d0, dd, rho0f, corr_rho, corr, a_extra, r);
+  if (r.flags & NF_FAR) return kNodeFar;
+  // every other node writes all its populations now (whole write sectors)
+  relax_store32<L, SHIFTED>(r, d0, dd, rho0f, beta, out);
+  if (r.flags & NF_REFINE) {
+    if (aprov) *aprov = r.alpha;
+    return kNodeRefine;
+  }
+  if (amap) *amap = r.alpha;
+  if (DIAG) diag32<L, SHIFTED, CHECK>(r, in, rho0, acc);
+  return kNodeDone;
+}
+
+// Second stage of one undecided node from its stored values in(i), after
+// the stream-collide kernel wrote it with the provisional alpha ap (NaN when
+// unknown: then the FP32 stage is run again to recover it): the
+// double-float decision (node32_refine), then the populations relaxed with
+// the decided alpha where they differ from the provisional ones, the alpha
+// map and the statistics.  Both relaxations use the double-float n, so a
+// population the decided alpha does not change at storage precision keeps
+// the provisional value, which differs from it by at most the rounding of
+// the FP32 n.  Returns false when the node is still undecided (left to the
+// FP64 path, which rewrites all of it).
+template <class L, bool SHIFTED, int DIAG, int CHECK, class In, class Out,
+          class Stat>
+__device__ __forceinline__ bool second_stage32(In in, float rho0f,
+                                               float beta, float corr_rho,
+                                               const float* __restrict__ corr,
+                                               float* amap, float ap, Out out,
+                                               Stat stat) {
+  constexpr int P = npairs<L>();
+  float d0, a_extra;
+  float2 dd[P];
+  load_deviations<L, SHIFTED>(in, rho0f, d0, dd, a_extra);
+  if (!(ap == ap)) {
+    N32<L> r;
+    node32_formula<L, SHIFTED>(d0, dd, rho0f, corr_rho, corr, a_extra, r);
+    ap = r.alpha;
+  }
+  N32<L> t;
+  t.flags = 0u;
+  t.alpha = 1.0f;
+  node32_refine<L, SHIFTED>(d0, dd, rho0f, corr_rho, corr, a_extra, t);
+  if (t.flags & NF_FAR) return false;
+  if (t.alpha != ap)
+    relax_update32<L, SHIFTED>(t, ap, t.alpha, d0, dd, rho0f, beta, out);
+  if (amap) *amap = t.alpha;
+  stat(t);
   return true;
+}
+
+// Buffer of undecided nodes for the second stage (SoA [Q + 2][cap]: the Q
+// stored values of a node, its key and its provisional alpha), written by
+// the stream-collide kernels and read by the fixup kernel, coalesced both
+// ways; a node that finds the buffer full goes to the deferred-node queue
+// tagged kTagRefine (the fixup then gathers it from f_in).  Every lane of
+// the warp calls; `mine` marks an undecided node, in(i) its stored values,
+// ap its provisional alpha.
+template <class L>
+__host__ __device__ constexpr int refine_rows() {
+  return L::Q + 2;
+}
+
+// Append the deferred nodes of a warp to the fixup queue with one atomic
+// per warp (every lane of the warp must call; st = kNodeDone for lanes
+// with nothing to defer).  The warp's entries are contiguous, so the
+// fixup's neighbouring threads gather neighbouring nodes.
+__device__ __forceinline__ void defer_nodes(unsigned* count, unsigned* queue,
+                                            unsigned cap, unsigned* err,
+                                            unsigned node, unsigned st) {
+  const unsigned mask = __ballot_sync(0xffffffffu, st != kNodeDone);
+  if (mask == 0u) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(mask) - 1;
+  unsigned base = 0u;
+  if (lane == leader) base = atomicAdd(count, (unsigned)__popc(mask));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (st != kNodeDone) {
+    const unsigned slot = base + (unsigned)__popc(mask & ((1u << lane) - 1u));
+    if (slot < cap)
+      queue[slot] = node | (st == kNodeRefine ? kTagRefine : 0u);
+    else
+      atomicOr(err, NF_BAD_NONFINITE);   // cannot happen: cap = n
+  }
 }
 
 // Same, with the values in a shared-memory column of stride TB.
 template <class L, bool SHIFTED, int DIAG, int CHECK, int TB, class Out>
-__device__ __forceinline__ bool sc32_node(const float* sm, float rho0f,
+__device__ __forceinline__ unsigned sc32_node(const float* sm, float rho0f,
                                           double rho0, float beta,
                                           float corr_rho,
                                           const float* __restrict__ corr,
-                                          float* amap, Acc32& acc, Out out) {
+                                          float* amap, Acc32& acc, Out out,
+                                          float* aprov = nullptr) {
   return sc32_node_in<L, SHIFTED, DIAG, CHECK>(
       [&](int i) { return sm[i * TB]; }, rho0f, rho0, beta, corr_rho, corr,
-      amap, acc, out);
+      amap, acc, out, aprov);
+}
+
+template <class L, class In>
+__device__ __forceinline__ void defer_undecided(const StepParams& p, bool mine,
+                                                In in, unsigned node,
+                                                float ap) {
+  if (p.refine_cap == 0u) {   // no buffer: the tagged queue and a gather
+    defer_nodes(&p.far_count[p.parity], p.far_queue, p.far_cap, p.err_flags,
+                node, mine ? kNodeRefine : kNodeDone);
+    return;
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, mine);
+  if (m == 0u) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  unsigned base = 0u;
+  if (lane == leader)
+    base = atomicAdd(&p.refine_count[p.parity], (unsigned)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (!mine) return;
+  const unsigned slot = base + (unsigned)__popc(m & ((1u << lane) - 1u));
+  if (slot < p.refine_cap) {
+    float* b = p.refine_buf + slot;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) b[(size_t)i * p.refine_cap] = in(i);
+    b[(size_t)L::Q * p.refine_cap] = __uint_as_float(node);
+    b[(size_t)(L::Q + 1) * p.refine_cap] = ap;
+  } else {
+    const unsigned q = atomicAdd(&p.far_count[p.parity], 1u);
+    if (q < p.far_cap)
+      p.far_queue[q] = node | kTagRefine;
+    else
+      atomicOr(p.err_flags, NF_BAD_NONFINITE);   // cannot happen: cap = n
+  }
 }
 
 template <class L, bool SHIFTED, int DIAG, int CHECK>
@@ -243,20 +435,20 @@ __global__ void __launch_bounds__(kSc32Threads, 2)
     const unsigned node = tile * kSc32Threads + threadIdx.x;
     const float* sm = smem + stage * Q * kSc32Threads + threadIdx.x;
     stage ^= 1;
-    if (node >= (unsigned)p.n) continue;
-    const bool done = sc32_node<L, SHIFTED, DIAG, CHECK, kSc32Threads>(
-        sm, rho0f, p.rho0, beta, p.corr_rho, p.corr,
-        p.alpha_map ? p.alpha_map + node : nullptr, acc,
-        [&](int i, float v) { p.out_pop[i][node] = v; });
-    if (!done) {
-      // far from (or invalid, or within FP32 noise of) equilibrium: the FP64
-      // fixup collides this node from f_in
-      const unsigned slot = atomicAdd(&p.far_count[p.parity], 1u);
-      if (slot < p.far_cap)
-        p.far_queue[slot] = node;
-      else
-        atomicOr(p.err_flags, NF_BAD_NONFINITE);   // cannot happen: cap = n
-    }
+    unsigned st = kNodeDone;
+    float ap = 0.0f;
+    if (node < (unsigned)p.n)
+      st = sc32_node<L, SHIFTED, DIAG, CHECK, kSc32Threads>(
+          sm, rho0f, p.rho0, beta, p.corr_rho, p.corr,
+          p.alpha_map ? p.alpha_map + node : nullptr, acc,
+          [&](int i, float v) { p.out_pop[i][node] = v; }, &ap);
+    // undecided (written provisionally): the fixup's second stage decides
+    defer_undecided<L>(p, st == kNodeRefine,
+                       [&](int i) { return sm[i * kSc32Threads]; }, node, ap);
+    // far from equilibrium or invalid: the FP64 fixup collides these nodes
+    // from f_in
+    defer_nodes(&p.far_count[p.parity], p.far_queue, p.far_cap, p.err_flags,
+                node, st == kNodeFar ? kNodeFar : kNodeDone);
   }
   cp_async_wait<0>();
   if (DIAG) store_acc32(acc, p.partials);

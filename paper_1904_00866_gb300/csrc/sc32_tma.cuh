@@ -181,14 +181,16 @@ __global__ void __launch_bounds__(256, 2) k_sc32_tma(const StepParams p) {
         }
       }
     }
-    const bool ok = sc32_node_in<L, true, DIAG, CHECK>(
+    const unsigned res = sc32_node_in<L, true, DIAG, CHECK>(
         [&](int i) { return v[i]; }, rho0f, p.rho0, beta, 0.0f, nullptr,
         p.alpha_map ? p.alpha_map + node : nullptr, acc,
         [&](int i, float val) { p.out_pop[i][node] = val; });
-    if (!ok) {
+    if (res != kNodeDone) {
+      // one atomic per node: a warp whose bounded wait ran out may leave
+      // the loop lane by lane, so no warp-wide vote here
       const unsigned slot = atomicAdd(&p.far_count[p.parity], 1u);
       if (slot < p.far_cap)
-        p.far_queue[slot] = node;
+        p.far_queue[slot] = node | (res == kNodeRefine ? kTagRefine : 0u);
       else
         atomicOr(p.err_flags, NF_BAD_NONFINITE);   // cannot happen: cap = n
     }

@@ -123,18 +123,15 @@ __global__ void __launch_bounds__(kWideThreads, 3)
     for (int h = 0; h < 2; ++h) {
       const int t = 32 * h + lane;
       const unsigned node = seg * kWideSeg + t;
-      const bool done = sc32_node_in<L, true, DIAG, CHECK>(
-          [&](int i) { return st[wide_base<L>(i) + wide_shift<L>(i) + t]; },
-          rho0f, p.rho0, beta, 0.0f, nullptr,
+      auto in = [&](int i) { return st[wide_base<L>(i) + wide_shift<L>(i) + t]; };
+      float ap = 0.0f;
+      const unsigned res = sc32_node_in<L, true, DIAG, CHECK>(
+          in, rho0f, p.rho0, beta, 0.0f, nullptr,
           p.alpha_map ? p.alpha_map + node : nullptr, acc,
-          [&](int i, float v) { p.out_pop[i][node] = v; });
-      if (!done) {
-        const unsigned slot = atomicAdd(&p.far_count[p.parity], 1u);
-        if (slot < p.far_cap)
-          p.far_queue[slot] = node;
-        else
-          atomicOr(p.err_flags, NF_BAD_NONFINITE);   // cannot happen: cap = n
-      }
+          [&](int i, float v) { p.out_pop[i][node] = v; }, &ap);
+      defer_undecided<L>(p, res == kNodeRefine, in, node, ap);
+      defer_nodes(&p.far_count[p.parity], p.far_queue, p.far_cap,
+                  p.err_flags, node, res == kNodeFar ? kNodeFar : kNodeDone);
     }
   }
   cp_async_wait<0>();

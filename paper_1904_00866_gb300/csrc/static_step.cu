@@ -80,6 +80,16 @@ extern "C" elbm_status elbm_step_static(
   if (e != cudaSuccess) return fail(ELBM_ECUDA, cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices)
     return fail(ELBM_EINVAL, "device ordinal out of range");
+  // Every stream-collide launcher sizes its grid to at most 8 resident
+  // blocks per SM, and the fixup uses at most 152 blocks; each block writes
+  // one diagnostic row.  Refuse before anything is queued if the rows could
+  // overflow the fixed array on this device.
+  int sms = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return fail(ELBM_ECUDA, cudaGetErrorString(e));
+  if ((long long)sms * 8 + 152 > kStaticMaxRows)
+    return fail(ELBM_EINVAL,
+                "device has too many SMs for the static diagnostic rows");
   unsigned char* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_mu);
@@ -141,9 +151,7 @@ extern "C" elbm_status elbm_step_static(
           ? launch_fp32_formula_d2q9(diag, 0, p, 0, 256, stream, &grid)
           : launch_fp32_formula_d3q27(diag, 0, p, 0, 256, stream, &grid);
   if (e != cudaSuccess) return fail(ELBM_ECUDA, cudaGetErrorString(e));
-  const int fgrid = grid < 152 ? grid : 152;
-  if (grid + fgrid > kStaticMaxRows)
-    return fail(ELBM_EINVAL, "grid exceeds the static diagnostic rows");
+  const int fgrid = grid < 152 ? grid : 152;   // grid + fgrid <= rows (above)
   StepParams pf = p;
   pf.partials = partials + (size_t)grid * NSTAT;
   e = lattice == ELBM_D2Q9 ? launch_far_d2q9(diag, 0, pf, fgrid, stream)
@@ -163,6 +171,10 @@ extern "C" elbm_status elbm_step_static(
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return fail(ELBM_ECUDA, cudaGetErrorString(e));
   stats_from_slots(slots, p.rho0, n, 0, 0, stats_out);
+  if (flags & NF_TIMEOUT)
+    return fail(ELBM_ECUDA,
+                "a bounded wait in the stream-collide kernel ran out; the "
+                "step is incomplete");
   if (flags & NF_BAD_NEG)
     return fail(ELBM_ENEGATIVE, "a node had a population <= 0");
   if (flags & NF_BAD_NONFINITE)

@@ -74,6 +74,12 @@ struct StepParams {
   // FP16 the pointers address binary16 arrays; the kernels cast them)
   const float* in_pop[27];
   float* out_pop[27];
+  // undecided nodes for the second stage: SoA [Q + 2][refine_cap] (stored
+  // values, node key, provisional alpha); refine_count[2] indexed by parity
+  // like far_count
+  float* refine_buf;
+  unsigned refine_cap;    // 0: none (undecided nodes use the tagged queue)
+  unsigned* refine_count;
 };
 
 template <class L>
@@ -196,51 +202,6 @@ __global__ void __launch_bounds__(256)
                     "FP32 / FP16 FORMULA runs in k_sc32 / k_sc16");
     }
   }
-  if (DIAG) acc.block_reduce_store(p.partials);
-}
-
-// FP64 collision of the nodes the FP32 / FP16 FORMULA kernel deferred (S:
-// the storage type, float or half_t).  Resets the other parity's counter
-// for the next step (stream order makes that counter idle here).
-template <class L, class S, int DIAG, int CHECK>
-__global__ void __launch_bounds__(256) k_far_fixup(const StepParams p) {
-  constexpr int Q = L::Q;
-  const unsigned count = min(p.far_count[p.parity], p.far_cap);
-  Acc acc;
-  acc.init();
-  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < count;
-       k += gridDim.x * blockDim.x) {
-    const long long node = p.far_queue[k];
-    const int x = (int)(node % p.nx);
-    const int y = (int)((node / p.nx) % p.ny);
-    const int z = (int)(node / ((long long)p.nx * p.ny));
-    Node64<L> nd;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const long long src = src_index<L>(p, i, x, y, z);
-      if constexpr (sizeof(S) == 2) {
-        nd.f[i] = h16_to_f<L>(
-            reinterpret_cast<const half_t*>(p.in_pop[i])[src], i, p.rho0);
-      } else {
-        const double v = (double)p.in_pop[i][src];
-        nd.f[i] = p.unshifted ? v : L::w(i) * p.rho0 + v;
-      }
-    }
-    auto store_s = [&](int i, double val) {
-      if (i < 0) {
-        p.alpha_map[node] = (float)val;
-      } else if constexpr (sizeof(S) == 2) {
-        reinterpret_cast<half_t*>(p.out_pop[i])[node] =
-            h16_from_dev<L>(val - L::w(i) * p.rho0, i);
-      } else {
-        p.out_pop[i][node] =
-            (float)(p.unshifted ? val : val - L::w(i) * p.rho0);
-      }
-    };
-    if (DIAG) acc.far += 1;
-    collide64<L, MODE_FORMULA, CHECK>(nd, p, true, acc, DIAG != 0, store_s);
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) p.far_count[p.parity ^ 1] = 0u;
   if (DIAG) acc.block_reduce_store(p.partials);
 }
 

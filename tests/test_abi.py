@@ -104,3 +104,28 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(e, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(ImportError):
         e.lib()
+
+
+def test_beta_comes_from_the_library(elbm):
+    """The binding reads beta from the C ABI; it matches the oracle's Eq. (2)
+    and needs no device."""
+    import oracle
+    L = elbm.lib()
+    h = ctypes.c_void_p()
+    for nu in (1e-5, 2.546e-3, 0.01, 0.5):
+        assert L.elbm_create(ctypes.byref(h), 1, 8, 8, 8, nu, 2) == 0
+        assert abs(L.elbm_beta(h) - oracle.beta_from_nu(nu)) <= 1e-15
+        L.elbm_destroy(h)
+    assert L.elbm_beta(None) != L.elbm_beta(None)        # NaN for NULL
+
+
+def test_binding_restates_no_method_arithmetic():
+    """The Python binding is marshalling only: no Eq. (2) (beta from nu) or
+    other method formula is evaluated there."""
+    src = open(os.path.join(ROOT, "paper_1904_00866_gb300",
+                            "__init__.py")).read()
+    code = re.sub(r'""".*?"""', "", src, flags=re.S)
+    code = "\n".join(l.split("#")[0] for l in code.splitlines())
+    for pattern in [r"1\.0\s*/\s*3", r"cs2", r"2\.0\s*\*\s*self\.nu",
+                    r"\bnp\.log", r"\bmath\.", r"\bsqrt\b"]:
+        assert not re.search(pattern, code), pattern
