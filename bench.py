@@ -86,6 +86,11 @@ def parse():
     ap.add_argument("--batch-every", type=int, default=1,
                     help="keep every k-th member of each lattice type of "
                          "the batched mix")
+    ap.add_argument("--decision", default="exact",
+                    choices=["exact", "certified"],
+                    help="FP32 entropy decisions not certified in FP32: "
+                         "retaken in double-float (exact, the default) or "
+                         "kept at the certified alpha")
     ap.add_argument("--storage", default="fp32_shifted",
                     choices=["fp32_shifted", "fp16_shifted"],
                     help="population storage of the timed lattice")
@@ -388,7 +393,7 @@ def serving(elbm, n_requests):
             r["lattice"], r["n"], r["seed"])
     fields = lambda lat, n, seed: cache[(lat, n, seed)]
     srv = serve.Server(elbm.Batch(burst=16), fields, budget_bytes=150e9,
-                       max_members=64, burst=16)
+                       max_members=256, burst=16)
     for r in reqs:
         srv.submit(r)
     rep = srv.run()
@@ -476,6 +481,7 @@ def run_elbm(args):
     fp16 = args.storage == "fp16_shifted"
     esize = 2 if fp16 else 4
     g = make_lattice(elbm, "D3Q27", n, args.storage, nu)
+    g.set_decision(args.decision)
     g.set_diagnostics(diag_every=args.diag_every)
     g.step(args.warmup, "formula")
     g.sync()

@@ -96,6 +96,24 @@ typedef enum {
   ELBM_ALPHA_SECANT = 2
 } elbm_alpha_mode;
 
+/* How FP32 / FP16 FORMULA steps decide a node whose FP32 entropy test is
+ * not certified (the sign of Delta H(2) or Delta H(1) within the FP32 error
+ * bound).
+ *   ELBM_DECISION_EXACT (default): a second stage recomputes f^eq - f in
+ *     double-float arithmetic and retakes the acceptance test after Eq. (8)
+ *     and Eq. (9) with that error bound (FP64 for the rare node still
+ *     undecided), so every node takes the branch the exact arithmetic
+ *     takes: alpha and the Fig. 5 counter are the paper's.
+ *   ELBM_DECISION_CERTIFIED: such a node keeps the certified alpha -- the
+ *     Eq. (9) chord on the upper bounds, rounded down, or 1 -- which also
+ *     satisfies H(f*(alpha)) <= H(f) and is within about 1e-5 of the exact
+ *     alpha; faster (no second stage).
+ * FP64 storage and the ROOT / SECANT modes are unaffected. */
+typedef enum {
+  ELBM_DECISION_EXACT = 0,
+  ELBM_DECISION_CERTIFIED = 1
+} elbm_decision;
+
 typedef enum {
   ELBM_OK = 0,
   ELBM_EINVAL = 1,      /* invalid argument                                */
@@ -175,6 +193,10 @@ ELBM_API elbm_status elbm_set_allocator(elbm_handle *h,
 ELBM_API elbm_status elbm_set_diagnostics(elbm_handle *h, int diag_every,
                                  int check_every, int alpha_map_every,
                                  int secant_iters);
+
+/* Decision mode of the FP32 / FP16 FORMULA steps (elbm_decision above).
+ * Takes effect from the next elbm_step. */
+ELBM_API elbm_status elbm_set_decision(elbm_handle *h, elbm_decision decision);
 
 /* f^0 = f^eq(rho, u) at every node.  rho: [nz][ny][nx] > 0,
  * u: [d][nz][ny][nx] with |u_a| < 1, FP64 host buffers.  Resets the step
@@ -376,6 +398,10 @@ ELBM_API elbm_status elbm_batch_alpha_map(elbm_batch *b, int id,
  * not evaluated in batches). */
 ELBM_API elbm_status elbm_batch_entropy_stats(elbm_batch *b, int id,
                                               elbm_entropy_stats_t *out);
+/* Decision of the FP32 entropy tests the first stage leaves undecided, as
+ * elbm_set_decision (default ELBM_DECISION_EXACT). */
+ELBM_API elbm_status elbm_batch_set_decision(elbm_batch *b,
+                                             elbm_decision decision);
 /* Launch configuration in use (after the first step: the tuned one). */
 ELBM_API elbm_status elbm_batch_tuning(const elbm_batch *b, int *threads,
                                        int *blocks_per_sm, int *burst);
@@ -387,6 +413,7 @@ ELBM_API double elbm_rho0(const elbm_handle *h);
 /* The beta of Eq. (2) the handle's steps use, c_s^2 / (2 nu + c_s^2) with
  * dt = 1 and c_s^2 = 1/3 (NaN for a NULL handle).  Needs no device. */
 ELBM_API double elbm_beta(const elbm_handle *h);
+
 
 #ifdef __cplusplus
 }

@@ -124,6 +124,7 @@ SIGNATURES = {
     "elbm_launch_count": (ctypes.c_longlong, []),
     "elbm_rho0": (ctypes.c_double, [_P]),
     "elbm_beta": (ctypes.c_double, [_P]),
+    "elbm_set_decision": (ctypes.c_int, [_P, ctypes.c_int]),
     "elbm_step_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_int,
                                         ctypes.c_double, ctypes.c_double, _P,
@@ -150,6 +151,7 @@ SIGNATURES = {
     "elbm_batch_alpha_map": (ctypes.c_int, [_P, ctypes.c_int, _FP]),
     "elbm_batch_entropy_stats": (ctypes.c_int, [_P, ctypes.c_int,
                                                 ctypes.POINTER(EntropyStats)]),
+    "elbm_batch_set_decision": (ctypes.c_int, [_P, ctypes.c_int]),
     "elbm_batch_tuning": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int)]),
@@ -302,6 +304,13 @@ class Lattice:
             raise ValueError("f must have Q * nx * ny * nz entries")
         self._check(lib().elbm_set_populations(self._h, _dptr(f)))
 
+    def set_decision(self, decision="exact"):
+        """'exact' (default): undecided FP32 entropy tests are retaken in
+        double-float arithmetic; 'certified': they keep the certified
+        alpha."""
+        d = {"exact": 0, "certified": 1}[decision]
+        self._check(lib().elbm_set_decision(self._h, d))
+
     def set_stream(self, stream):
         self._check(lib().elbm_set_stream(self._h, _P(int(stream))))
 
@@ -447,6 +456,11 @@ class Batch:
         self._check(lib().elbm_batch_set_options(
             self._h, int(diag_every), int(burst), int(bool(use_graphs)),
             int(bool(autotune))))
+
+    def set_decision(self, decision="exact"):
+        """As Lattice.set_decision, for every member."""
+        d = {"exact": 0, "certified": 1}[decision]
+        self._check(lib().elbm_batch_set_decision(self._h, d))
 
     def add(self, lattice, nx, ny, nz, nu, rho, u):
         lat = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)

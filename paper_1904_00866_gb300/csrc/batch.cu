@@ -3,7 +3,7 @@
 // A batch owns up to kBatchMaxMembers independent periodic lattices
 // (FP32-shifted storage, FORMULA alpha), each with its own type, size and
 // viscosity, and advances them in bursts of steps.  A burst is launched as a
-// captured CUDA graph (k_batch + k_batch_fixup per step) when its length
+// captured CUDA graph (k_batch, k_batch_refine, k_batch_fixup per step) when its length
 // equals the tuned burst length, else as direct launches.  The member table
 // and tile prefix are copied to the device before each burst; the graph
 // reads them at run time, so it stays valid when members come and go.
@@ -104,6 +104,17 @@ cudaError_t launch_batch(int tb, int diag, const BatchParams& bp, int grid,
               : launch_batch_kernel<256, 0>(bp, grid, s);
 }
 
+cudaError_t launch_batch_refine(int diag, const BatchParams& bp, int blocks,
+                                cudaStream_t s) {
+  if (blocks > kMaxRefineBlocks) return cudaErrorInvalidValue;
+  if (diag)
+    k_batch_refine<1><<<152, 256, 0, s>>>(bp, blocks);
+  else
+    k_batch_refine<0><<<152, 256, 0, s>>>(bp, blocks);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_batch_fixup(int diag, const BatchParams& bp,
                                cudaStream_t s) {
   if (diag)
@@ -173,9 +184,11 @@ struct elbm_batch {
   size_t tmem_cap = 0;
   int* d_count = nullptr;
   MemberStats* d_stats = nullptr;
-  unsigned* d_far_count = nullptr;   // [0..1] deferred, [2..3] undecided
+  unsigned* d_far_count = nullptr;   // [2] deferred nodes by step parity
   float* d_refine = nullptr;         // undecided-node buffer
   unsigned refine_cap = 0;
+  unsigned* d_refine_counts = nullptr;   // entries per batch-kernel block
+  int exact = 1;                         // second stage of undecided nodes
   unsigned* d_err = nullptr;
   unsigned long long* d_queue = nullptr;
   size_t queue_cap = 0;
@@ -244,8 +257,10 @@ static elbm_status ensure_tables(elbm_batch* b) {
   b->d_stats = (MemberStats*)balloc(b, sizeof(MemberStats) * kBatchMaxMembers);
   b->d_far_count = (unsigned*)balloc(b, 256);
   b->d_err = (unsigned*)balloc(b, 256);
+  b->d_refine_counts =
+      (unsigned*)balloc(b, sizeof(unsigned) * kMaxRefineBlocks);
   if (!b->d_desc || !b->d_begin || !b->d_count || !b->d_stats ||
-      !b->d_far_count || !b->d_err)
+      !b->d_far_count || !b->d_err || !b->d_refine_counts)
     return bfail(b, ELBM_ENOMEM, "batch table allocation failed");
   cudaMemsetAsync(b->d_err, 0, 256, b->stream);
   cudaMemsetAsync(b->d_far_count, 0, 256, b->stream);
@@ -298,7 +313,8 @@ static BatchParams batch_params(elbm_batch* b) {
   bp.far_count = b->d_far_count;
   bp.refine_buf = b->d_refine;
   bp.refine_cap = b->refine_cap;
-  bp.refine_count = b->d_far_count + 2;
+  bp.refine_counts = b->d_refine_counts;
+  bp.exact = b->exact;
   bp.err_flags = b->d_err;
   bp.step = 0;
   return bp;
@@ -378,7 +394,7 @@ static elbm_status upload_tables(elbm_batch* b) {
     e = cudaMemcpyAsync(b->d_count, &count, sizeof(int),
                         cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess)
-    e = cudaMemsetAsync(b->d_far_count, 0, 4 * sizeof(unsigned), b->stream);
+    e = cudaMemsetAsync(b->d_far_count, 0, 2 * sizeof(unsigned), b->stream);
   // the sources are pageable host memory: each copy is staged before the
   // call returns, so the host tables may be rebuilt right away
   if (e != cudaSuccess) return bfail(b, ELBM_ECUDA, cudaGetErrorString(e));
@@ -407,12 +423,16 @@ static cudaError_t run_steps(elbm_batch* b, int nsteps, int diag, int grid) {
   // autotuner's dry steps, which all run as step 0, would never clear
   // counter 0 and its stale entries would pile up.
   cudaError_t e0 =
-      cudaMemsetAsync(b->d_far_count, 0, 4 * sizeof(unsigned), b->stream);
+      cudaMemsetAsync(b->d_far_count, 0, 2 * sizeof(unsigned), b->stream);
   if (e0 != cudaSuccess) return e0;
   for (int s = 0; s < nsteps; ++s) {
     bp.step = s;
     cudaError_t e = launch_batch(b->tb, diag, bp, grid, b->stream);
     if (e != cudaSuccess) return e;
+    if (bp.exact) {
+      e = launch_batch_refine(diag, bp, grid, b->stream);
+      if (e != cudaSuccess) return e;
+    }
     e = launch_batch_fixup(diag, bp, b->stream);
     if (e != cudaSuccess) return e;
   }
@@ -540,6 +560,7 @@ void elbm_batch_destroy(elbm_batch* b) {
   bfree(b, b->d_count, 256);
   bfree(b, b->d_stats, sizeof(MemberStats) * kBatchMaxMembers);
   bfree(b, b->d_far_count, 256);
+  bfree(b, b->d_refine_counts, sizeof(unsigned) * kMaxRefineBlocks);
   bfree(b, b->d_refine, sizeof(float) * kBatchRefineRows * (size_t)b->refine_cap);
   bfree(b, b->d_err, 256);
   delete b;
@@ -768,7 +789,7 @@ elbm_status elbm_batch_step(elbm_batch* b, long long nsteps) {
         b->exec_diag = diag;
       }
       e = cudaGraphLaunch(b->exec, b->stream);
-      count_launches(2 * b->burst);
+      count_launches((b->exact ? 3 : 2) * b->burst);   // launches per step
     } else {
       e = run_steps(b, steps_here, diag, grid);
     }
@@ -919,6 +940,16 @@ elbm_status elbm_batch_entropy_stats(elbm_batch* b, int id,
   out->n_band = (long long)s.band;
   out->n_far = (long long)s.far;
   out->n_degenerate = (long long)s.degen;
+  return ELBM_OK;
+}
+
+elbm_status elbm_batch_set_decision(elbm_batch* b, elbm_decision decision) {
+  if (!b) return ELBM_EINVAL;
+  if (decision != ELBM_DECISION_EXACT && decision != ELBM_DECISION_CERTIFIED)
+    return bfail(b, ELBM_EINVAL, "unknown decision mode");
+  const int exact = decision == ELBM_DECISION_EXACT;
+  if (exact != b->exact) drop_graph(b);   // the graph's launches differ
+  b->exact = exact;
   return ELBM_OK;
 }
 

@@ -64,11 +64,13 @@ struct BatchParams {
   int step;                     // step index within the burst
   // undecided nodes for the second stage: SoA [27 + 3][refine_cap] (the
   // member's Q stored values, then node and member index as bits and the
-  // provisional alpha);
-  // refine_count[2] indexed like far_count
+  // provisional alpha); block b of a launch of G blocks owns the segment of
+  // refine_cap / G entries from b (refine_cap / G) on and writes how many
+  // it used to refine_counts[b]
   float* refine_buf;
   unsigned refine_cap;
-  unsigned* refine_count;
+  unsigned* refine_counts;
+  int exact;                    // 0: undecided nodes keep the certified alpha
 };
 constexpr int kBatchRefineRows = 27 + 3;
 
@@ -167,6 +169,9 @@ __global__ void __launch_bounds__(TB, 2048 / TB / 4)
   // the member descriptors are read on every tile: stage them in shared
   // memory once (word copy; MemberDesc is trivially copyable)
   MemberDesc* s_desc = reinterpret_cast<MemberDesc*>(smem + 2 * 27 * TB);
+  __shared__ unsigned s_refine;   // this block's undecided-node entries
+  if (threadIdx.x == 0) s_refine = 0u;
+  const unsigned seg = bp.refine_cap / gridDim.x;
   const int count = *bp.count;
   for (int k = threadIdx.x; k <= count; k += TB) s_begin[k] = bp.tile_begin[k];
   {
@@ -224,11 +229,13 @@ __global__ void __launch_bounds__(TB, 2048 / TB / 4)
       if (m.lattice == 1)
         res = sc32_node<D3Q27, true, DIAG, 0, TB>(sm, m.rho0f, m.rho0, m.beta,
                                                   0.0f, nullptr, amap, acc,
-                                                  store, &ap);
+                                                  store,
+                                                  bp.exact ? &ap : nullptr);
       else
         res = sc32_node<D2Q9, true, DIAG, 0, TB>(sm, m.rho0f, m.rho0, m.beta,
                                                  0.0f, nullptr, amap, acc,
-                                                 store, &ap);
+                                                 store,
+                                                 bp.exact ? &ap : nullptr);
     }
     {
       // undecided nodes (written provisionally) into the second-stage
@@ -239,15 +246,13 @@ __global__ void __launch_bounds__(TB, 2048 / TB / 4)
         const int lane = threadIdx.x & 31;
         const int leader = __ffs(um) - 1;
         unsigned base = 0u;
-        if (lane == leader)
-          base = atomicAdd(&bp.refine_count[bp.step & 1],
-                           (unsigned)__popc(um));
+        if (lane == leader) base = atomicAdd(&s_refine, (unsigned)__popc(um));
         base = __shfl_sync(0xffffffffu, base, leader);
         if (res == kNodeRefine) {
           const unsigned slot =
               base + (unsigned)__popc(um & ((1u << lane) - 1u));
-          if (slot < bp.refine_cap) {
-            float* rb = bp.refine_buf + slot;
+          if (slot < seg) {
+            float* rb = bp.refine_buf + (size_t)blockIdx.x * seg + slot;
             const int q = m.lattice == 1 ? 27 : 9;
             for (int i = 0; i < q; ++i)
               rb[(size_t)i * bp.refine_cap] = sm[i * TB];
@@ -287,33 +292,111 @@ __global__ void __launch_bounds__(TB, 2048 / TB / 4)
     }
   }
   cp_async_wait<0>();
+  __syncthreads();
+  if (threadIdx.x == 0) bp.refine_counts[blockIdx.x] = min(s_refine, seg);
 }
 
-// Deferred nodes of the batch kernel: the double-float second stage for
-// nodes whose FP32 decision was not certified, the FP64 FORMULA for the
-// others and for the still undecided; clears the other parity's counter for
-// the next step.
+// Statistics of one node collided by a fixup kernel, added to its member's
+// record (on the member's statistics step).
+__device__ __forceinline__ void member_stats_add(const BatchParams& bp, int mi,
+                                                 const MemberDesc& m,
+                                                 const Acc& acc, bool fp64) {
+  if (!(m.diag && bp.step == m.steps_left - 1 && acc.nodes > 0)) return;
+  MemberStats* st = bp.stats + mi;
+  atomicAdd(&st->drho, acc.drho);
+  atomicAdd(&st->j0, acc.j0);
+  atomicAdd(&st->j1, acc.j1);
+  atomicAdd(&st->j2, acc.j2);
+  atomicAdd(&st->ke, acc.ke);
+  atomicAdd(&st->asum, acc.asum);
+  atomicAdd(&st->nodes, 1ull);
+  if (fp64) atomicAdd(&st->far, 1ull);
+  atomicAdd(&st->acc2, (unsigned long long)acc.acc2);
+  atomicAdd(&st->formula, (unsigned long long)acc.formula);
+  atomicAdd(&st->band, (unsigned long long)acc.band);
+  atomicAdd(&st->degen, (unsigned long long)acc.degen);
+  const float a = (float)acc.asum;
+  atomicMin(&st->amin_bits, __float_as_uint(a));
+  atomicMax(&st->amax_bits, __float_as_uint(a));
+}
+
+// Second stage of the undecided nodes the batch kernel (`blocks` blocks)
+// buffered; a node it leaves undecided joins the deferred-node queue for
+// the FP64 fixup that follows.
+template <int DIAG>
+__global__ void __launch_bounds__(256) k_batch_refine(const BatchParams bp,
+                                                      int blocks) {
+  __shared__ unsigned pre[kMaxRefineBlocks + 1];
+  for (int b = threadIdx.x; b < blocks; b += blockDim.x)
+    pre[b + 1] = bp.refine_counts[b];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    pre[0] = 0u;
+    for (int b = 1; b <= blocks; ++b) pre[b] += pre[b - 1];
+  }
+  __syncthreads();
+  const unsigned total = pre[blocks];
+  const unsigned seg = bp.refine_cap / (unsigned)blocks;
+  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < total;
+       k += gridDim.x * blockDim.x) {
+    int lo = 0, hi = blocks;   // pre[lo] <= k < pre[lo + 1]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (pre[mid] <= k)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    const float* rb = bp.refine_buf + (size_t)lo * seg + (k - pre[lo]);
+    const unsigned node = __float_as_uint(rb[(size_t)27 * bp.refine_cap]);
+    const int mi = (int)__float_as_uint(rb[(size_t)28 * bp.refine_cap]);
+    const float ap = rb[(size_t)29 * bp.refine_cap];
+    const MemberDesc& m = bp.members[mi];
+    float* out = pick(m, m.parity0 + bp.step + 1);
+    StepParams pp;
+    pp.beta = m.beta64;
+    pp.rho0 = m.rho0;
+    pp.alpha_map = m.alpha_map;
+    pp.unshifted = 0;
+    pp.corr_rho = 0.0f;
+    Acc acc;
+    acc.init();
+    bool done;
+    auto run = [&](auto lat) {
+      using L = decltype(lat);
+      float v[L::Q];
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) v[i] = rb[(size_t)i * bp.refine_cap];
+      return refine_deferred<L, true, DIAG, 0>(
+          pp, v, node, ap, acc,
+          [&](int i, float val) { out[(size_t)i * m.n + node] = val; });
+    };
+    done = m.lattice == 1 ? run(D3Q27{}) : run(D2Q9{});
+    if (!done) {
+      const unsigned q = atomicAdd(&bp.far_count[bp.step & 1], 1u);
+      if (q < bp.far_cap)
+        bp.far_queue[q] = ((unsigned long long)mi << 32) | node;
+      else
+        atomicOr(bp.err_flags, NF_BAD_NONFINITE);   // cannot happen
+    } else if (DIAG) {
+      member_stats_add(bp, mi, m, acc, false);
+    }
+  }
+}
+
+// FP64 fixup of the batch kernel's deferred-node queue (values gathered
+// from the member's buffer): the FP64 FORMULA, after the second stage for
+// entries tagged kTagRefine (a full buffer segment); clears the other
+// parity's counter for the next step.
 template <int DIAG>
 __global__ void __launch_bounds__(256) k_batch_fixup(const BatchParams bp) {
-  const unsigned rcount =
-      bp.refine_cap ? min(bp.refine_count[bp.step & 1], bp.refine_cap) : 0u;
   const unsigned count = min(bp.far_count[bp.step & 1], bp.far_cap);
-  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < rcount + count;
+  // entries dealt round-robin over the blocks (see k_far_fixup)
+  for (unsigned k = threadIdx.x * gridDim.x + blockIdx.x; k < count;
        k += gridDim.x * blockDim.x) {
-    int mi;
-    unsigned tagged;
-    const float* rb = nullptr;   // the node's stored values in the buffer
-    float ap = __int_as_float(0x7fc00000);   // NaN: provisional alpha unknown
-    if (k < rcount) {
-      rb = bp.refine_buf + k;
-      ap = rb[(size_t)29 * bp.refine_cap];
-      tagged = __float_as_uint(rb[(size_t)27 * bp.refine_cap]) | kTagRefine;
-      mi = (int)__float_as_uint(rb[(size_t)28 * bp.refine_cap]);
-    } else {
-      const unsigned long long e = bp.far_queue[k - rcount];
-      mi = (int)(e >> 32);
-      tagged = (unsigned)(e & 0xffffffffu);
-    }
+    const unsigned long long e = bp.far_queue[k];
+    const int mi = (int)(e >> 32);
+    const unsigned tagged = (unsigned)(e & 0xffffffffu);
     const unsigned node = tagged & ~kTagRefine;
     const MemberDesc& m = bp.members[mi];
     const float* in = pick(m, m.parity0 + bp.step);
@@ -341,11 +424,12 @@ __global__ void __launch_bounds__(256) k_batch_fixup(const BatchParams bp) {
       float v[L::Q];
 #pragma unroll
       for (int i = 0; i < L::Q; ++i)
-        v[i] = rb ? rb[(size_t)i * bp.refine_cap]
-                  : in[(size_t)i * m.n + src_index<L>(g, i, x, y, z)];
+        v[i] = in[(size_t)i * m.n + src_index<L>(g, i, x, y, z)];
       auto store32 = [&](int i, float val) { out[(size_t)i * m.n + node] = val; };
       if ((tagged & kTagRefine) &&
-          refine_deferred<L, true, DIAG, 0>(pp, v, node, ap, acc, store32))
+          refine_deferred<L, true, DIAG, 0>(pp, v, node,
+                                            __int_as_float(0x7fc00000), acc,
+                                            store32))
         return;
       fp64 = true;
       Node64<L> nd;
@@ -364,29 +448,9 @@ __global__ void __launch_bounds__(256) k_batch_fixup(const BatchParams bp) {
       run(D3Q27{});
     else
       run(D2Q9{});
-    if (DIAG && m.diag && bp.step == m.steps_left - 1 && acc.nodes > 0) {
-      MemberStats* st = bp.stats + mi;
-      atomicAdd(&st->drho, acc.drho);
-      atomicAdd(&st->j0, acc.j0);
-      atomicAdd(&st->j1, acc.j1);
-      atomicAdd(&st->j2, acc.j2);
-      atomicAdd(&st->ke, acc.ke);
-      atomicAdd(&st->asum, acc.asum);
-      atomicAdd(&st->nodes, 1ull);
-      if (fp64) atomicAdd(&st->far, 1ull);
-      atomicAdd(&st->acc2, (unsigned long long)acc.acc2);
-      atomicAdd(&st->formula, (unsigned long long)acc.formula);
-      atomicAdd(&st->band, (unsigned long long)acc.band);
-      atomicAdd(&st->degen, (unsigned long long)acc.degen);
-      const float a = (float)acc.asum;
-      atomicMin(&st->amin_bits, __float_as_uint(a));
-      atomicMax(&st->amax_bits, __float_as_uint(a));
-    }
+    if (DIAG) member_stats_add(bp, mi, m, acc, fp64);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    bp.far_count[(bp.step & 1) ^ 1] = 0u;
-    if (bp.refine_count) bp.refine_count[(bp.step & 1) ^ 1] = 0u;
-  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) bp.far_count[(bp.step & 1) ^ 1] = 0u;
 }
 
 }  // namespace elbm

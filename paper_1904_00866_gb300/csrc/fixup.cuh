@@ -1,20 +1,16 @@
-// Fixup kernel of the FP32 / FP16 FORMULA step: collides the nodes the
-// stream-collide kernel deferred, reading f_in (unchanged during the step)
-// and writing f_out.
-//
-// Entries come from the undecided-node buffer (coalesced) and from the
-// deferred-node queue; two kinds of entries:
-//   * nodes whose FP32 entropy decision was not certified (tagged
-//     kTagRefine; the kernel wrote them with a provisional alpha): the
-//     second stage recomputes f^eq - f in double-float arithmetic, decides
-//     with its much smaller error bound (node32_refine) and rewrites the
-//     populations the decided alpha changes; the rare node still undecided
-//     falls through to
-//   * FP64: nodes far from equilibrium (max |x_i| > 1/8, |u| >= 1/2),
-//     invalid states, and the undecided rest, collided by the FP64 FORMULA
-//     (Eqs. (8)-(9) with logarithms), alpha rounded down to FP32.
-// Resets the other parity's counter for the next step (stream order makes
-// that counter idle here).
+// Fixup kernels of the FP32 / FP16 FORMULA step, after the stream-collide
+// kernel; both read f_in (unchanged during the step) and write f_out.
+//   k_refine_stage: the second stage of the nodes whose FP32 entropy
+//     decision was not certified (the stream-collide kernel wrote them with
+//     the certified alpha and put their stored values in a buffer): f^eq - f
+//     recomputed in double-float arithmetic, the decision retaken with its
+//     much smaller error bound (node32_refine), and the populations the
+//     decided alpha changes rewritten.
+//   k_far_fixup: the FP64 FORMULA (Eqs. (8)-(9) with logarithms, alpha
+//     rounded down to FP32) for nodes far from equilibrium (max |x_i| > 1/8,
+//     |u| >= 1/2), invalid states and the rare node the second stage left
+//     undecided.  It also resets the other parity's counter for the next
+//     step (stream order makes that counter idle here).
 #pragma once
 #include "sc32.cuh"
 
@@ -48,50 +44,108 @@ __device__ __forceinline__ bool refine_deferred(const StepParams& p,
       });
 }
 
-// S: the storage type (float or half_t).  Entries [0, rcount) come from the
-// undecided-node buffer (values stored there, read coalesced), the rest
-// from the deferred-node queue (values gathered from f_in).
+// Second stage of the undecided nodes in the buffer (S: the storage type,
+// float or half_t).  Block b of the stream-collide launch (`blocks`
+// blocks) wrote refine_counts[b] entries from b (refine_cap / blocks) on;
+// every
+// block of this kernel forms their prefix sums in shared memory and takes
+// entries k with a grid stride.  The double-float stage decides (and
+// rewrites the populations its alpha changes); a node it leaves undecided
+// joins the deferred-node queue, so the FP64 fixup that follows collides
+// it with full warps instead of one lane of a warp here.
 template <class L, class S, int DIAG, int CHECK>
-__global__ void __launch_bounds__(256) k_far_fixup(const StepParams p) {
+__global__ void __launch_bounds__(256, 2) k_refine_stage(const StepParams p,
+                                                         int blocks) {
   constexpr int Q = L::Q;
-  const unsigned rcount =
-      p.refine_cap ? min(p.refine_count[p.parity], p.refine_cap) : 0u;
-  const unsigned fcount = min(p.far_count[p.parity], p.far_cap);
+  __shared__ unsigned pre[kMaxRefineBlocks + 1];
+  for (int b = threadIdx.x; b < blocks; b += blockDim.x)
+    pre[b + 1] = p.refine_counts[b];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    pre[0] = 0u;
+    for (int b = 1; b <= blocks; ++b) pre[b] += pre[b - 1];
+  }
+  __syncthreads();
+  const unsigned total = pre[blocks];
+  const unsigned seg = p.refine_cap / (unsigned)blocks;
   const bool shifted = sizeof(S) == 2 || !p.unshifted;
   Acc acc;
   acc.init();
-  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < rcount + fcount;
+  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < total;
        k += gridDim.x * blockDim.x) {
-    float v[Q];
-    long long node;
-    bool refine;
-    float ap = __int_as_float(0x7fc00000);   // NaN: provisional alpha unknown
-    if (k < rcount) {
-      const float* b = p.refine_buf + k;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) v[i] = b[(size_t)i * p.refine_cap];
-      node = __float_as_uint(b[(size_t)Q * p.refine_cap]);
-      ap = b[(size_t)(Q + 1) * p.refine_cap];
-      refine = true;
-    } else {
-      const unsigned e = p.far_queue[k - rcount];
-      node = e & ~kTagRefine;
-      refine = (e & kTagRefine) != 0u;
-      const int x = (int)(node % p.nx);
-      const int y = (int)((node / p.nx) % p.ny);
-      const int z = (int)(node / ((long long)p.nx * p.ny));
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const long long src = src_index<L>(p, i, x, y, z);
-        if constexpr (sizeof(S) == 2)
-          v[i] = h16_dev<L>(reinterpret_cast<const unsigned short*>(
-                                p.in_pop[i])[src],
-                            i);
-        else
-          v[i] = p.in_pop[i][src];
-      }
+    int lo = 0, hi = blocks;   // pre[lo] <= k < pre[lo + 1]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (pre[mid] <= k)
+        lo = mid;
+      else
+        hi = mid;
     }
-    if (refine) {
+    const float* b =
+        p.refine_buf + (size_t)lo * seg + (k - pre[lo]);
+    float v[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) v[i] = b[(size_t)i * p.refine_cap];
+    const long long node = __float_as_uint(b[(size_t)Q * p.refine_cap]);
+    const float ap = b[(size_t)(Q + 1) * p.refine_cap];
+    bool done;
+    if constexpr (sizeof(S) == 2) {
+      done = refine_deferred<L, true, DIAG, CHECK>(
+          p, v, node, ap, acc, [&](int i, float val) {
+            reinterpret_cast<unsigned short*>(p.out_pop[i])[node] =
+                h16_bits<L>(val, i);
+          });
+    } else {
+      auto out = [&](int i, float val) { p.out_pop[i][node] = val; };
+      done = shifted ? refine_deferred<L, true, DIAG, CHECK>(p, v, node, ap,
+                                                             acc, out)
+                     : refine_deferred<L, false, DIAG, CHECK>(p, v, node, ap,
+                                                              acc, out);
+    }
+    if (!done) {
+      const unsigned q = atomicAdd(&p.far_count[p.parity], 1u);
+      if (q < p.far_cap)
+        p.far_queue[q] = (unsigned)node;
+      else
+        atomicOr(p.err_flags, NF_BAD_NONFINITE);   // cannot happen: cap = n
+    }
+  }
+  if (DIAG) acc.block_reduce_store(p.partials);
+}
+
+// FP64 fixup (S: the storage type, float or half_t): the deferred-node
+// queue, with values gathered from f_in.  Entries tagged kTagRefine (a
+// full buffer segment, or no buffer) take the second stage here first.
+template <class L, class S, int DIAG, int CHECK>
+__global__ void __launch_bounds__(256) k_far_fixup(const StepParams p) {
+  constexpr int Q = L::Q;
+  const unsigned count = min(p.far_count[p.parity], p.far_cap);
+  const bool shifted = sizeof(S) == 2 || !p.unshifted;
+  Acc acc;
+  acc.init();
+  // entries dealt round-robin over the blocks: a short queue of FP64 nodes
+  // (each ~1,500 FP64 instructions) spreads over every SM instead of
+  // filling the first few
+  for (unsigned k = threadIdx.x * gridDim.x + blockIdx.x; k < count;
+       k += gridDim.x * blockDim.x) {
+    const unsigned e = p.far_queue[k];
+    const long long node = e & ~kTagRefine;
+    const int x = (int)(node % p.nx);
+    const int y = (int)((node / p.nx) % p.ny);
+    const int z = (int)(node / ((long long)p.nx * p.ny));
+    float v[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const long long src = src_index<L>(p, i, x, y, z);
+      if constexpr (sizeof(S) == 2)
+        v[i] = h16_dev<L>(reinterpret_cast<const unsigned short*>(
+                              p.in_pop[i])[src],
+                          i);
+      else
+        v[i] = p.in_pop[i][src];
+    }
+    if (e & kTagRefine) {
+      const float ap = __int_as_float(0x7fc00000);   // NaN: recomputed
       bool done;
       if constexpr (sizeof(S) == 2) {
         done = refine_deferred<L, true, DIAG, CHECK>(
@@ -129,10 +183,7 @@ __global__ void __launch_bounds__(256) k_far_fixup(const StepParams p) {
     if (DIAG) acc.far += 1;
     collide64<L, MODE_FORMULA, CHECK>(nd, p, true, acc, DIAG != 0, store_s);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    p.far_count[p.parity ^ 1] = 0u;
-    if (p.refine_count) p.refine_count[p.parity ^ 1] = 0u;
-  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) p.far_count[p.parity ^ 1] = 0u;
   if (DIAG) acc.block_reduce_store(p.partials);
 }
 

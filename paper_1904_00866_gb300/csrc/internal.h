@@ -44,6 +44,11 @@ void stats_from_slots(const double* slots, double rho0, long long n,
                                         cudaStream_t s, int* grid_used);      \
   cudaError_t launch_far16_##LAT(int diag, int check, const StepParams& p,   \
                                  int grid, cudaStream_t s);                  \
+  cudaError_t launch_refine_##LAT(int diag, int check, const StepParams& p,  \
+                                  int blocks, int grid, cudaStream_t s);     \
+  cudaError_t launch_refine16_##LAT(int diag, int check,                     \
+                                    const StepParams& p, int blocks,         \
+                                    int grid, cudaStream_t s);               \
   cudaError_t launch_fp16_fp64mode_##LAT(int mode, int diag, int check,      \
                                          const StepParams& p, int grid,       \
                                          int block, cudaStream_t s,           \

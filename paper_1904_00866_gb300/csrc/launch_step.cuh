@@ -264,4 +264,22 @@ static cudaError_t launch_far_lattice(int diag, int check,
   return cudaGetLastError();
 }
 
+// Second stage of the undecided nodes a stream-collide launch of `blocks`
+// blocks buffered (S: storage type).
+template <class L, class S = float>
+static cudaError_t launch_refine_lattice(int diag, int check,
+                                         const StepParams& p, int blocks,
+                                         int grid, cudaStream_t s) {
+  if (blocks > kMaxRefineBlocks) return cudaErrorInvalidValue;
+  if (grid <= 0) grid = 152;
+  if (check)
+    k_refine_stage<L, S, 1, 1><<<grid, 256, 0, s>>>(p, blocks);
+  else if (diag)
+    k_refine_stage<L, S, 1, 0><<<grid, 256, 0, s>>>(p, blocks);
+  else
+    k_refine_stage<L, S, 0, 0><<<grid, 256, 0, s>>>(p, blocks);
+  count_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace elbm

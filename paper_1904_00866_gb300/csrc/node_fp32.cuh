@@ -232,6 +232,20 @@ __device__ __forceinline__ int decide32(const DH32& h, float& alpha) {
   return kChord;
 }
 
+// The certified alpha of an undecided node: the Eq. (9) chord evaluated on
+// the upper bounds and rounded down when Delta H(1) + e1 < 0 (the chord
+// root decreases in both values, so it stays at or below the exact Eq. (9)
+// value, itself at or below the root of Eq. (4)), else 1 (f* = f^eq, for
+// which H(f*) <= H(f) holds exactly).
+__device__ __forceinline__ float certified_alpha32(const DH32& h) {
+  const float D2hi = __fadd_ru(h.D2, h.e2);
+  const float D1hi = __fadd_ru(h.D1, h.e1);
+  if (!(D1hi < 0.0f) || !(D2hi > 0.0f)) return 1.0f;
+  const float den = __fsub_rd(D2hi, D1hi);
+  const float tt = __fmul_ru(__fdividef(D2hi, den), 1.0f + 2.384185791e-7f);
+  return __fsub_rd(2.0f, tt);
+}
+
 // Mass and momentum sums of the deviations, exact as double-floats.  Each
 // delta = hi + mid + lo with hi on the 2^-20 grid, mid on the 2^-40 grid and
 // |lo| <= 2^-41 (all three splits exact); with sum_i |delta_i| < 4 the hi
@@ -454,7 +468,8 @@ __device__ __forceinline__ void node32_refine(
 template <class L, bool SHIFTED>
 __device__ __forceinline__ void node32_formula(
     float d0, const float2 (&dd)[npairs<L>()], float rho0, float corr_rho,
-    const float* __restrict__ corr, float a_extra, N32<L>& r) {
+    const float* __restrict__ corr, float a_extra, N32<L>& r,
+    bool exact = false) {
   constexpr int Q = L::Q;
   constexpr int P = npairs<L>();
   constexpr float uu = 5.9604645e-8f;  // 2^-24
@@ -587,9 +602,10 @@ __device__ __forceinline__ void node32_formula(
   }
   if (xabs == 0.0f) {
     // f^eq == f in FP32 only: the exact state may still differ from its
-    // equilibrium below FP32 resolution; the second stage decides (the
-    // provisional alpha is immaterial: n = 0 leaves f unchanged)
-    r.flags = NF_REFINE;
+    // equilibrium below FP32 resolution; the second stage decides.  The
+    // provisional alpha = 1 (f* = f^eq) keeps H(f*) <= H(f) exactly; the
+    // relaxation leaves f unchanged either way (n = 0).
+    r.flags = NF_REFINE | NF_DEGENERATE;
     r.alpha = 1.0f;
     return;
   }
@@ -652,14 +668,22 @@ __device__ __forceinline__ void node32_formula(
   float alpha = 2.0f;
   const int k = decide32(h, alpha);
   if (k == kUndecided) {
-    // the sign of Delta H(2) or of Delta H(1) is within the FP32 error:
-    // the second stage (node32_refine) decides.  The provisional alpha
-    // follows the nominal FP32 values; the populations written with it
-    // are replaced where the decided alpha changes them.
-    r.flags = NF_REFINE;
-    r.alpha = h.D2 <= 0.0f
-                  ? 2.0f
-                  : (h.D1 < 0.0f ? 2.0f - __fdividef(h.D2, h.D2 - h.D1) : 1.0f);
+    // The sign of Delta H(2) or of Delta H(1) is within the FP32 error.
+    // Without a second stage (exact false) the node takes the certified
+    // alpha -- the Eq. (9) chord on the upper bounds, rounded down, when
+    // Delta H(1) + e1 < 0, else 1 (f* = f^eq) -- for which
+    // H(f*(alpha)) <= H(f) holds too.  With it, the node is written
+    // provisionally with the nominal FP32 decision (alpha = 2 when
+    // Delta H(2) <= 0, else the chord of the nominal values), which the
+    // second stage (node32_refine) usually confirms, so that few
+    // populations need rewriting.
+    r.flags = NF_REFINE | NF_BAND;
+    r.alpha = exact ? (h.D2 <= 0.0f
+                           ? 2.0f
+                           : (h.D1 < 0.0f
+                                  ? 2.0f - __fdividef(h.D2, h.D2 - h.D1)
+                                  : 1.0f))
+                    : certified_alpha32(h);
     return;
   }
   r.alpha = alpha;

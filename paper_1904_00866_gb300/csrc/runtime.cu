@@ -135,6 +135,8 @@ struct elbm_handle {
   unsigned* far_queue = nullptr;
   float* refine_buf = nullptr;     // undecided-node buffer [q + 2][cap]
   unsigned refine_cap = 0;
+  unsigned* refine_counts = nullptr;   // per stream-collide block
+  int exact = 1;                   // second stage of undecided decisions
   long long step = 0;
   int diag_every = 1, check_every = 0, amap_every = 0, secant_iters = 4;
   bool stats_valid = false;
@@ -218,7 +220,7 @@ static elbm_status ensure_buffers(elbm_handle* h) {
   const size_t fb = (size_t)h->q * pop_stride(h) * elem_size(h->dtype);
   h->f[0] = dev_alloc(h, fb);
   h->f[1] = dev_alloc(h, fb);
-  h->partial_rows_max = 2 * max_grid_rows();
+  h->partial_rows_max = 3 * max_grid_rows();
   h->partials =
       (double*)dev_alloc(h, sizeof(double) * NSTAT * h->partial_rows_max);
   h->stats_dev = (double*)dev_alloc(h, sizeof(double) * NSTAT);
@@ -233,7 +235,9 @@ static elbm_status ensure_buffers(elbm_handle* h) {
         std::min<long long>(h->n, std::max<long long>(h->n / 16, 65536));
     h->refine_buf = (float*)dev_alloc(
         h, sizeof(float) * (size_t)(h->q + 2) * (size_t)cap);
-    h->refine_cap = h->refine_buf ? (unsigned)cap : 0u;
+    h->refine_counts =
+        (unsigned*)dev_alloc(h, sizeof(unsigned) * kMaxRefineBlocks);
+    h->refine_cap = h->refine_buf && h->refine_counts ? (unsigned)cap : 0u;
   }
   if (!h->f[0] || !h->f[1] || !h->partials || !h->stats_dev ||
       !h->err_flags || !h->far_count ||
@@ -563,12 +567,13 @@ elbm_status elbm_step(elbm_handle* h, long long nsteps, elbm_alpha_mode mode) {
   p.far_count = h->far_count;
   p.far_queue = h->far_queue;
   p.far_cap = h->far_queue ? (unsigned)h->n : 0u;
+  p.exact = h->exact;
   p.refine_buf = h->refine_buf;
   p.refine_cap = h->refine_cap;
-  p.refine_count = h->far_count + 2;
+  p.refine_counts = h->refine_counts;
   // the deferred-node counters start every call at zero; within the call
   // each step's fixup clears the counter the next step uses
-  if (nsteps > 0) cudaMemsetAsync(h->far_count, 0, 4 * sizeof(unsigned),
+  if (nsteps > 0) cudaMemsetAsync(h->far_count, 0, 2 * sizeof(unsigned),
                                   h->stream);
   const bool d2 = h->lattice == ELBM_D2Q9;
   // 0: FP64, 1: FP32 (shifted or not), 2: FP16-shifted
@@ -632,10 +637,23 @@ elbm_status elbm_step(elbm_handle* h, long long nsteps, elbm_alpha_mode mode) {
     int rows = grid;
     if (fp32_formula) {
       StepParams pf = p;
-      pf.partials = h->partials + (size_t)grid * NSTAT;
-      // as many blocks as the step: the second stage of undecided nodes
-      // runs here too, and its gathers want the parallelism
       const int fgrid = grid;
+      if (p.exact && p.refine_cap) {
+        // second stage of the undecided nodes the step buffered
+        pf.partials = h->partials + (size_t)rows * NSTAT;
+        e = storage == 2
+                ? (d2 ? launch_refine16_d2q9(diag, check, pf, grid, fgrid,
+                                             h->stream)
+                      : launch_refine16_d3q27(diag, check, pf, grid, fgrid,
+                                              h->stream))
+                : (d2 ? launch_refine_d2q9(diag, check, pf, grid, fgrid,
+                                           h->stream)
+                      : launch_refine_d3q27(diag, check, pf, grid, fgrid,
+                                            h->stream));
+        if (e != cudaSuccess) return cuda_fail(h, e, "second stage launch");
+        rows += fgrid;
+      }
+      pf.partials = h->partials + (size_t)rows * NSTAT;
       if (storage == 2)
         e = d2 ? launch_far16_d2q9(diag, check, pf, fgrid, h->stream)
                : launch_far16_d3q27(diag, check, pf, fgrid, h->stream);
@@ -805,6 +823,14 @@ long long elbm_launch_count(void) { return g_launches.load(); }
 double elbm_rho0(const elbm_handle* h) { return h ? h->rho0 : 0.0; }
 
 double elbm_beta(const elbm_handle* h) { return h ? h->beta : NAN; }
+
+elbm_status elbm_set_decision(elbm_handle* h, elbm_decision decision) {
+  if (!h) return ELBM_EINVAL;
+  if (decision != ELBM_DECISION_EXACT && decision != ELBM_DECISION_CERTIFIED)
+    return fail(h, ELBM_EINVAL, "unknown decision mode");
+  h->exact = decision == ELBM_DECISION_EXACT;
+  return ELBM_OK;
+}
 
 elbm_status elbm_set_profiling(elbm_handle* h, int enable) {
   if (!h) return ELBM_EINVAL;

@@ -53,6 +53,8 @@ __global__ void __launch_bounds__(kSc32Threads, 2)
   const float beta = (float)p.beta;
   Acc32 acc;
   if (DIAG) acc.init();
+  __shared__ unsigned s_refine;     // this block's undecided-node entries
+  refine_block_begin(&s_refine);
 
   unsigned tile = blockIdx.x;
   int stage = 0;
@@ -89,12 +91,14 @@ __global__ void __launch_bounds__(kSc32Threads, 2)
             reinterpret_cast<unsigned short*>(p.out_pop[i])[node] =
                 h16_bits<L>(v, i);
           },
-          &ap);
-    defer_undecided<L>(p, st == kNodeRefine, in, node, ap);
+          p.exact ? &ap : nullptr);
+    if (p.exact)
+      defer_undecided<L>(p, &s_refine, st == kNodeRefine, in, node, ap);
     defer_nodes(&p.far_count[p.parity], p.far_queue, p.far_cap, p.err_flags,
                 node, st == kNodeFar ? kNodeFar : kNodeDone);
   }
   cp_async_wait<0>();
+  refine_block_end(p, &s_refine);
   if (DIAG) store_acc32(acc, p.partials);
 }
 

@@ -263,10 +263,12 @@ __device__ __forceinline__ void diag32(const N32<L>& r, In in, double rho0,
 // Collision of one node whose Q gathered values are returned by in(i)
 // (shared memory).  Writes the Q post-collision values through
 // out(i, value) and the alpha through amap (nullable).  Returns kNodeDone;
-// kNodeRefine for a node whose FP32 decision is undecided (populations
-// written with the provisional alpha, no statistics or alpha map: the
-// second stage completes it); or kNodeFar (nothing written: the FP64 fixup
-// collides it).
+// kNodeRefine for a node whose FP32 decision is undecided when the caller
+// runs the second stage (aprov non-null: populations written with the
+// certified alpha, stored in *aprov; no statistics or alpha map -- the
+// second stage completes the node); or kNodeFar (nothing written: the FP64
+// fixup collides it).  With aprov null an undecided node keeps its
+// certified alpha.
 template <class L, bool SHIFTED, int DIAG, int CHECK, class In, class Out>
 __device__ __forceinline__ unsigned sc32_node_in(
     In in, float rho0f, double rho0, float beta, float corr_rho,
@@ -277,13 +279,18 @@ __device__ __forceinline__ unsigned sc32_node_in(
   float2 dd[P];
   load_deviations<L, SHIFTED>(in, rho0f, d0, dd, a_extra);
   N32<L> r;
-  node32_formula<L, SHIFTED>(d0, dd, rho0f, corr_rho, corr, a_extra, r);
+  node32_formula<L, SHIFTED>(d0, dd, rho0f, corr_rho, corr, a_extra, r,
+                             aprov != nullptr);
   if (r.flags & NF_FAR) return kNodeFar;
   // every other node writes all its populations now (whole write sectors)
   relax_store32<L, SHIFTED>(r, d0, dd, rho0f, beta, out);
   if (r.flags & NF_REFINE) {
-    if (aprov) *aprov = r.alpha;
-    return kNodeRefine;
+    if (aprov) {   // the second stage completes the node
+      *aprov = r.alpha;
+      return kNodeRefine;
+    }
+    // without a second stage the certified alpha is final
+    r.flags = (r.flags & NF_DEGENERATE) ? NF_DEGENERATE : NF_FORMULA | NF_BAND;
   }
   if (amap) *amap = r.alpha;
   if (DIAG) diag32<L, SHIFTED, CHECK>(r, in, rho0, acc);
@@ -313,7 +320,8 @@ __device__ __forceinline__ bool second_stage32(In in, float rho0f,
   load_deviations<L, SHIFTED>(in, rho0f, d0, dd, a_extra);
   if (!(ap == ap)) {
     N32<L> r;
-    node32_formula<L, SHIFTED>(d0, dd, rho0f, corr_rho, corr, a_extra, r);
+    node32_formula<L, SHIFTED>(d0, dd, rho0f, corr_rho, corr, a_extra, r,
+                               true);
     ap = r.alpha;
   }
   N32<L> t;
@@ -377,10 +385,12 @@ __device__ __forceinline__ unsigned sc32_node(const float* sm, float rho0f,
 }
 
 template <class L, class In>
-__device__ __forceinline__ void defer_undecided(const StepParams& p, bool mine,
-                                                In in, unsigned node,
-                                                float ap) {
-  if (p.refine_cap == 0u) {   // no buffer: the tagged queue and a gather
+__device__ __forceinline__ void defer_undecided(const StepParams& p,
+                                                unsigned* block_count,
+                                                bool mine, In in,
+                                                unsigned node, float ap) {
+  const unsigned seg = p.refine_cap / gridDim.x;   // this block's segment
+  if (seg == 0u) {   // no buffer: the tagged queue and a gather
     defer_nodes(&p.far_count[p.parity], p.far_queue, p.far_cap, p.err_flags,
                 node, mine ? kNodeRefine : kNodeDone);
     return;
@@ -390,13 +400,12 @@ __device__ __forceinline__ void defer_undecided(const StepParams& p, bool mine,
   const int lane = threadIdx.x & 31;
   const int leader = __ffs(m) - 1;
   unsigned base = 0u;
-  if (lane == leader)
-    base = atomicAdd(&p.refine_count[p.parity], (unsigned)__popc(m));
+  if (lane == leader) base = atomicAdd(block_count, (unsigned)__popc(m));
   base = __shfl_sync(0xffffffffu, base, leader);
   if (!mine) return;
   const unsigned slot = base + (unsigned)__popc(m & ((1u << lane) - 1u));
-  if (slot < p.refine_cap) {
-    float* b = p.refine_buf + slot;
+  if (slot < seg) {
+    float* b = p.refine_buf + (size_t)blockIdx.x * seg + slot;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) b[(size_t)i * p.refine_cap] = in(i);
     b[(size_t)L::Q * p.refine_cap] = __uint_as_float(node);
@@ -410,16 +419,32 @@ __device__ __forceinline__ void defer_undecided(const StepParams& p, bool mine,
   }
 }
 
+// Block prologue / epilogue of the buffer: the block's entry counter in
+// shared memory starts at zero; at the end the number of entries the block
+// wrote goes to refine_counts[blockIdx.x] (0 when unused).
+__device__ __forceinline__ void refine_block_begin(unsigned* block_count) {
+  if (threadIdx.x == 0) *block_count = 0u;
+  __syncthreads();
+}
+__device__ __forceinline__ void refine_block_end(const StepParams& p,
+                                                 const unsigned* block_count) {
+  __syncthreads();
+  if (threadIdx.x == 0 && p.refine_counts)
+    p.refine_counts[blockIdx.x] = min(*block_count, p.refine_cap / gridDim.x);
+}
+
 template <class L, bool SHIFTED, int DIAG, int CHECK>
 __global__ void __launch_bounds__(kSc32Threads, 2)
     k_sc32(const StepParams p) {
   constexpr int Q = L::Q;
   extern __shared__ float smem[];   // [2][Q][256]
+  __shared__ unsigned s_refine;     // this block's undecided-node entries
   const unsigned ntiles = (unsigned)((p.n + kSc32Threads - 1) / kSc32Threads);
   const float rho0f = (float)p.rho0;
   const float beta = (float)p.beta;
   Acc32 acc;
   if (DIAG) acc.init();
+  refine_block_begin(&s_refine);
 
   unsigned tile = blockIdx.x;
   int stage = 0;
@@ -441,16 +466,21 @@ __global__ void __launch_bounds__(kSc32Threads, 2)
       st = sc32_node<L, SHIFTED, DIAG, CHECK, kSc32Threads>(
           sm, rho0f, p.rho0, beta, p.corr_rho, p.corr,
           p.alpha_map ? p.alpha_map + node : nullptr, acc,
-          [&](int i, float v) { p.out_pop[i][node] = v; }, &ap);
-    // undecided (written provisionally): the fixup's second stage decides
-    defer_undecided<L>(p, st == kNodeRefine,
-                       [&](int i) { return sm[i * kSc32Threads]; }, node, ap);
+          [&](int i, float v) { p.out_pop[i][node] = v; },
+          p.exact ? &ap : nullptr);
+    // undecided (written with the certified alpha): the second stage
+    // decides
+    if (p.exact)
+      defer_undecided<L>(p, &s_refine, st == kNodeRefine,
+                         [&](int i) { return sm[i * kSc32Threads]; }, node,
+                         ap);
     // far from equilibrium or invalid: the FP64 fixup collides these nodes
     // from f_in
     defer_nodes(&p.far_count[p.parity], p.far_queue, p.far_cap, p.err_flags,
                 node, st == kNodeFar ? kNodeFar : kNodeDone);
   }
   cp_async_wait<0>();
+  refine_block_end(p, &s_refine);
   if (DIAG) store_acc32(acc, p.partials);
 }
 

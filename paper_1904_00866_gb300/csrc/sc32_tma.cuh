@@ -181,10 +181,12 @@ __global__ void __launch_bounds__(256, 2) k_sc32_tma(const StepParams p) {
         }
       }
     }
+    float ap = 0.0f;   // this variant sends undecided nodes to the queue
     const unsigned res = sc32_node_in<L, true, DIAG, CHECK>(
         [&](int i) { return v[i]; }, rho0f, p.rho0, beta, 0.0f, nullptr,
         p.alpha_map ? p.alpha_map + node : nullptr, acc,
-        [&](int i, float val) { p.out_pop[i][node] = val; });
+        [&](int i, float val) { p.out_pop[i][node] = val; },
+        p.exact ? &ap : nullptr);
     if (res != kNodeDone) {
       // one atomic per node: a warp whose bounded wait ran out may leave
       // the loop lane by lane, so no warp-wide vote here
@@ -201,6 +203,7 @@ __global__ void __launch_bounds__(256, 2) k_sc32_tma(const StepParams p) {
     // too, so they get there as well)
     for (int st = 0; st < S; ++st) mbar_wait_bounded(&full[st], 0u);
   }
+  if (threadIdx.x == 0 && p.refine_counts) p.refine_counts[blockIdx.x] = 0u;
   if (DIAG) store_acc32(acc, p.partials);
 }
 

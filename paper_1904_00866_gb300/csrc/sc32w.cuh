@@ -104,6 +104,8 @@ __global__ void __launch_bounds__(kWideThreads, 3)
   const float beta = (float)p.beta;
   Acc32 acc;
   if (DIAG) acc.init();
+  __shared__ unsigned s_refine;     // this block's undecided-node entries
+  refine_block_begin(&s_refine);
 
   unsigned seg = blockIdx.x * kWideWarps + w;
   int stage = 0;
@@ -128,13 +130,16 @@ __global__ void __launch_bounds__(kWideThreads, 3)
       const unsigned res = sc32_node_in<L, true, DIAG, CHECK>(
           in, rho0f, p.rho0, beta, 0.0f, nullptr,
           p.alpha_map ? p.alpha_map + node : nullptr, acc,
-          [&](int i, float v) { p.out_pop[i][node] = v; }, &ap);
-      defer_undecided<L>(p, res == kNodeRefine, in, node, ap);
+          [&](int i, float v) { p.out_pop[i][node] = v; },
+          p.exact ? &ap : nullptr);
+      if (p.exact)
+        defer_undecided<L>(p, &s_refine, res == kNodeRefine, in, node, ap);
       defer_nodes(&p.far_count[p.parity], p.far_queue, p.far_cap,
                   p.err_flags, node, res == kNodeFar ? kNodeFar : kNodeDone);
     }
   }
   cp_async_wait<0>();
+  refine_block_end(p, &s_refine);
   if (DIAG) store_acc32(acc, p.partials);
 }
 

@@ -142,6 +142,9 @@ extern "C" elbm_status elbm_step_static(
   p.rho0 = (double)(float)rho0;
   p.unshifted = 0;
   p.secant_iters = 1;
+  // the exact decision of elbm_step's default; without a buffer the
+  // undecided nodes take the fixup's gathering path
+  p.exact = 1;
   p.div_nx.init((unsigned)nx);
   p.div_ny.init((unsigned)ny);
 

@@ -21,4 +21,8 @@ cudaError_t launch_fp16_fp64mode_d2q9(int mode, int diag, int check,
   return launch_diag<D2Q9, half_t, MODE_ROOT>(diag, check, p, grid, block, s,
                                               grid_used);
 }
+cudaError_t launch_refine16_d2q9(int diag, int check, const StepParams& p,
+                                  int blocks, int grid, cudaStream_t s) {
+  return launch_refine_lattice<D2Q9, half_t>(diag, check, p, blocks, grid, s);
+}
 }  // namespace elbm

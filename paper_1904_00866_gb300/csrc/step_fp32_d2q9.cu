@@ -12,4 +12,8 @@ cudaError_t launch_far_d2q9(int diag, int check, const StepParams& p, int grid,
                              cudaStream_t s) {
   return launch_far_lattice<D2Q9>(diag, check, p, grid, s);
 }
+cudaError_t launch_refine_d2q9(int diag, int check, const StepParams& p,
+                                int blocks, int grid, cudaStream_t s) {
+  return launch_refine_lattice<D2Q9>(diag, check, p, blocks, grid, s);
+}
 }  // namespace elbm

@@ -12,4 +12,8 @@ cudaError_t launch_far_d3q27(int diag, int check, const StepParams& p, int grid,
                              cudaStream_t s) {
   return launch_far_lattice<D3Q27>(diag, check, p, grid, s);
 }
+cudaError_t launch_refine_d3q27(int diag, int check, const StepParams& p,
+                                int blocks, int grid, cudaStream_t s) {
+  return launch_refine_lattice<D3Q27>(diag, check, p, blocks, grid, s);
+}
 }  // namespace elbm

@@ -47,6 +47,10 @@ struct FastDiv {
   }
 };
 
+// Largest stream-collide grid whose undecided-node buffer segments the
+// second stage reads (8 resident blocks on each of up to 256 SMs).
+constexpr int kMaxRefineBlocks = 2048;
+
 struct StepParams {
   const void* f_in;
   void* f_out;
@@ -74,12 +78,16 @@ struct StepParams {
   // FP16 the pointers address binary16 arrays; the kernels cast them)
   const float* in_pop[27];
   float* out_pop[27];
-  // undecided nodes for the second stage: SoA [Q + 2][refine_cap] (stored
-  // values, node key, provisional alpha); refine_count[2] indexed by parity
-  // like far_count
+  // Second stage of undecided FP32 decisions (exact: 1; certified: 0, the
+  // certified alpha is final).  Its buffer is SoA [Q + 2][refine_cap]
+  // (stored values, node key, provisional alpha); block b of a
+  // stream-collide launch of G blocks owns the segment of
+  // refine_cap / G entries from b (refine_cap / G) on and writes how many
+  // it used to refine_counts[b].
+  int exact;
   float* refine_buf;
-  unsigned refine_cap;    // 0: none (undecided nodes use the tagged queue)
-  unsigned* refine_count;
+  unsigned refine_cap;    // 0: no buffer (undecided nodes use the queue)
+  unsigned* refine_counts;
 };
 
 template <class L>

@@ -193,11 +193,16 @@ def test_fp32_taylor_green_3d_vs_fp64_oracle(elbm, orc):
     assert s["n_violations"] == 0 and s["checked"] == 1
 
 
+@pytest.mark.parametrize("decision", ["exact", "certified"])
 @pytest.mark.parametrize("lat,shape,nu", [("D2Q9", (1, 64, 64), 1e-5),
                                           ("D3Q27", (12, 16, 20), 1e-4)])
-def test_fp32_single_step_alpha_against_fp64(elbm, orc, lat, shape, nu):
+def test_fp32_single_step_alpha_against_fp64(elbm, orc, lat, shape, nu,
+                                             decision):
     """One FP32 FORMULA step from an evolved state: per-node alpha vs the
-    FP64 FORMULA alpha of the same stored state, and populations."""
+    FP64 FORMULA alpha of the same stored state, and populations.  The
+    exact decision takes the FP64 branch (acceptance of alpha = 2 or the
+    Eq. (9) chord) at every node; the certified one never exceeds the FP64
+    alpha."""
     nz, ny, nx = shape
     if lat == "D2Q9":
         rho, u = W.shear_layer(nx, ny=ny)
@@ -207,6 +212,7 @@ def test_fp32_single_step_alpha_against_fp64(elbm, orc, lat, shape, nu):
     o.init_fields(rho, u)
     o.step(60)
     g = elbm.Lattice(lat, nx, ny, nz, nu=nu, dtype="fp32_shifted")
+    g.set_decision(decision)
     g.set_populations(o.f)
     g.set_diagnostics(diag_every=1, check_every=1, alpha_map_every=1)
     loaded = g.populations()          # the state as the GPU stores it
@@ -215,6 +221,17 @@ def test_fp32_single_step_alpha_against_fp64(elbm, orc, lat, shape, nu):
     g.step(1, "formula")
     ag = g.alpha_map().astype(np.float64)
     ao = amaps[0]
+    s = g.entropy_stats()
+    assert s["n_violations"] == 0 and s["checked"] == 1
+    if decision == "exact":
+        # the same branch as the FP64 decision at every node, alpha within
+        # the FP32 evaluation of the chord (the accepted 2 exactly)
+        assert s["n_decision_mismatch"] == 0
+        assert np.all((ao == 2.0) == (ag == 2.0))
+        assert np.abs(ag - ao).max() < 2e-5
+        f = g.populations()
+        assert np.all(np.abs(f - o.f) <= 2e-6 * np.abs(o.f))
+        return
     assert np.all(ag <= ao + 1e-12)
     # nodes whose non-equilibrium part is resolved in FP32 (rms x > 1e-5)
     # follow the FP64 alpha to 1e-4; nodes within FP32 noise of equilibrium
@@ -231,8 +248,6 @@ def test_fp32_single_step_alpha_against_fp64(elbm, orc, lat, shape, nu):
     close = (ao - ag) <= 1e-4
     assert close[resolved].mean() >= 0.999, close[resolved].mean()
     assert np.all((ag[~resolved] == 1.0) | close[~resolved])
-    s = g.entropy_stats()
-    assert s["n_violations"] == 0 and s["checked"] == 1
     assert s["n_decision_mismatch"] <= s["n_band"]
     f = g.populations()
     assert np.all(np.abs(f - o.f) <= 2e-6 * np.abs(o.f))
