@@ -291,11 +291,11 @@ static elbm_status ensure_queue(elbm_batch* b) {
   // undecided-node buffer: a sixteenth of the queue, at least 65,536
   // entries (a full buffer falls back to the gathering queue)
   bfree(b, b->d_refine,
-        sizeof(float) * kBatchRefineRows * (size_t)b->refine_cap);
+        sizeof(float) * kBatchRecord * (size_t)b->refine_cap);
   const size_t rcap =
       std::min<size_t>(0xffffffffu, std::max<size_t>(cap / 16, 65536));
   b->d_refine =
-      (float*)balloc(b, sizeof(float) * kBatchRefineRows * rcap);
+      (float*)balloc(b, sizeof(float) * kBatchRecord * rcap);
   b->refine_cap = b->d_refine ? (unsigned)rcap : 0u;
   return ELBM_OK;
 }
@@ -561,7 +561,7 @@ void elbm_batch_destroy(elbm_batch* b) {
   bfree(b, b->d_stats, sizeof(MemberStats) * kBatchMaxMembers);
   bfree(b, b->d_far_count, 256);
   bfree(b, b->d_refine_counts, sizeof(unsigned) * kMaxRefineBlocks);
-  bfree(b, b->d_refine, sizeof(float) * kBatchRefineRows * (size_t)b->refine_cap);
+  bfree(b, b->d_refine, sizeof(float) * kBatchRecord * (size_t)b->refine_cap);
   bfree(b, b->d_err, 256);
   delete b;
 }

@@ -62,17 +62,17 @@ struct BatchParams {
   unsigned* far_count;          // [2]
   unsigned* err_flags;
   int step;                     // step index within the burst
-  // undecided nodes for the second stage: SoA [27 + 3][refine_cap] (the
-  // member's Q stored values, then node and member index as bits and the
-  // provisional alpha); block b of a launch of G blocks owns the segment of
-  // refine_cap / G entries from b (refine_cap / G) on and writes how many
-  // it used to refine_counts[b]
+  // undecided nodes for the second stage: records of kBatchRecord floats
+  // (the member's Q stored values from float 0, then node and member index
+  // as bits and the provisional alpha at floats 28, 29, 30); block b of a
+  // launch of G blocks owns the segment of refine_cap / G records from
+  // b (refine_cap / G) on and writes how many it used to refine_counts[b]
   float* refine_buf;
   unsigned refine_cap;
   unsigned* refine_counts;
   int exact;                    // 0: undecided nodes keep the certified alpha
 };
-constexpr int kBatchRefineRows = 27 + 3;
+constexpr int kBatchRecord = 32;   // floats per undecided-node record
 
 __device__ __forceinline__ float* pick(const MemberDesc& m, int parity) {
   return (parity & 1) ? m.buf[1] : m.buf[0];
@@ -252,13 +252,16 @@ __global__ void __launch_bounds__(TB, 2048 / TB / 4)
           const unsigned slot =
               base + (unsigned)__popc(um & ((1u << lane) - 1u));
           if (slot < seg) {
-            float* rb = bp.refine_buf + (size_t)blockIdx.x * seg + slot;
+            float4* rec = reinterpret_cast<float4*>(
+                bp.refine_buf +
+                ((size_t)blockIdx.x * seg + slot) * (size_t)kBatchRecord);
             const int q = m.lattice == 1 ? 27 : 9;
-            for (int i = 0; i < q; ++i)
-              rb[(size_t)i * bp.refine_cap] = sm[i * TB];
-            rb[(size_t)27 * bp.refine_cap] = __uint_as_float(node);
-            rb[(size_t)28 * bp.refine_cap] = __uint_as_float((unsigned)mi);
-            rb[(size_t)29 * bp.refine_cap] = ap;
+            auto val = [&](int k) { return k < q ? sm[k * TB] : 0.0f; };
+            for (int j = 0; j < (q + 3) / 4; ++j)
+              rec[j] = make_float4(val(4 * j), val(4 * j + 1), val(4 * j + 2),
+                                   val(4 * j + 3));
+            rec[7] = make_float4(__uint_as_float(node),
+                                 __uint_as_float((unsigned)mi), ap, 0.0f);
             res = kNodeDone;
           }
         }
@@ -347,10 +350,12 @@ __global__ void __launch_bounds__(256) k_batch_refine(const BatchParams bp,
       else
         hi = mid;
     }
-    const float* rb = bp.refine_buf + (size_t)lo * seg + (k - pre[lo]);
-    const unsigned node = __float_as_uint(rb[(size_t)27 * bp.refine_cap]);
-    const int mi = (int)__float_as_uint(rb[(size_t)28 * bp.refine_cap]);
-    const float ap = rb[(size_t)29 * bp.refine_cap];
+    const float4* rec = reinterpret_cast<const float4*>(
+        bp.refine_buf + ((size_t)lo * seg + (k - pre[lo])) * (size_t)kBatchRecord);
+    const float4 tail = rec[7];
+    const unsigned node = __float_as_uint(tail.x);
+    const int mi = (int)__float_as_uint(tail.y);
+    const float ap = tail.z;
     const MemberDesc& m = bp.members[mi];
     float* out = pick(m, m.parity0 + bp.step + 1);
     StepParams pp;
@@ -364,11 +369,18 @@ __global__ void __launch_bounds__(256) k_batch_refine(const BatchParams bp,
     bool done;
     auto run = [&](auto lat) {
       using L = decltype(lat);
-      float v[L::Q];
+      float v[L::Q + 3];
 #pragma unroll
-      for (int i = 0; i < L::Q; ++i) v[i] = rb[(size_t)i * bp.refine_cap];
+      for (int j = 0; j < (L::Q + 3) / 4; ++j) {
+        const float4 t = rec[j];
+        v[4 * j] = t.x;
+        if (4 * j + 1 < L::Q + 3) v[4 * j + 1] = t.y;
+        if (4 * j + 2 < L::Q + 3) v[4 * j + 2] = t.z;
+        if (4 * j + 3 < L::Q + 3) v[4 * j + 3] = t.w;
+      }
+      float (&vq)[L::Q] = *reinterpret_cast<float (*)[L::Q]>(v);
       return refine_deferred<L, true, DIAG, 0>(
-          pp, v, node, ap, acc,
+          pp, vq, node, ap, acc,
           [&](int i, float val) { out[(size_t)i * m.n + node] = val; });
     };
     done = m.lattice == 1 ? run(D3Q27{}) : run(D2Q9{});

@@ -81,13 +81,23 @@ __global__ void __launch_bounds__(256, 2) k_refine_stage(const StepParams p,
       else
         hi = mid;
     }
-    const float* b =
-        p.refine_buf + (size_t)lo * seg + (k - pre[lo]);
+    constexpr int R = refine_record<L>();
+    const float4* rec = reinterpret_cast<const float4*>(
+        p.refine_buf + ((size_t)lo * seg + (k - pre[lo])) * (size_t)R);
+    float w[R];
+#pragma unroll
+    for (int j = 0; j < R / 4; ++j) {
+      const float4 t = rec[j];
+      w[4 * j] = t.x;
+      w[4 * j + 1] = t.y;
+      w[4 * j + 2] = t.z;
+      w[4 * j + 3] = t.w;
+    }
     float v[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) v[i] = b[(size_t)i * p.refine_cap];
-    const long long node = __float_as_uint(b[(size_t)Q * p.refine_cap]);
-    const float ap = b[(size_t)(Q + 1) * p.refine_cap];
+    for (int i = 0; i < Q; ++i) v[i] = w[i];
+    const long long node = __float_as_uint(w[Q]);
+    const float ap = w[Q + 1];
     bool done;
     if constexpr (sizeof(S) == 2) {
       done = refine_deferred<L, true, DIAG, CHECK>(

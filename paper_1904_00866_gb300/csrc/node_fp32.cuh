@@ -437,18 +437,28 @@ __device__ __forceinline__ void node32_refine(
     return;
   }
   // Error of x_i: the rounding of n_i to FP32, of f_i and of the quotient
-  // (6.1 u |x_i|) plus the double-float error of n_i, at most
-  // W_i rho (1 + Dd)^3 2^-37 (per-axis factors within 2^-40, products and
-  // the final sums within 8 u^2 of their magnitudes), divided by
-  // f_i >= W_i rho / G.
+  // (6.1 u |x_i|) plus the double-float error of n_i divided by
+  // f_i >= W_i rho / G.  With e = u^2 and |u_a| <= U < 1/2: u within
+  // 23 e U (corrected quotient), s within 40 e s <= 60 e U^2 (one Newton
+  // step from a 9.5 u value), d = +-3u + 2s within 93 e U + 144 e U^2 (with
+  // its sum's rounding), 1 + d within c e, c = 8 + 117 U + 168 U^2; the
+  // D-fold product P within (1 + Dd)^D (3c + 16) e, rho P - rho0 (rho within
+  // 3 e rho), the product with W_i and the difference with delta_i add
+  // 36 e (1 + Dd)^D + 25 e rho0 / rho in units of W_i rho and 8 e |delta_i|;
+  // |delta_i| <= f_i + W_i rho0.  The bound below doubles that sum.
   constexpr float kUp = 1.00000095367431640625f;   // 1 + 2^-20
+  constexpr float e2u = 3.5527136788005009e-15f;   // u^2 = 2^-48
   const float Dd = fmaf(3.0f * U, U, 3.0f * U);
   const float omd = 1.0f - Dd;
   const float omdD = L::D == 3 ? omd * omd * omd : omd * omd;
   const float G = __fdividef(1.0f + xabs, omdD) * kUp;
-  const float opd3 = (1.0f + Dd) * (1.0f + Dd) * (1.0f + Dd);
-  const float Ex = 1.01f * (6.1f * uu * xabs +
-                            G * (opd3 * 7.275957614183426e-12f + a_extra));
+  const float opdD = L::D == 3 ? (1.0f + Dd) * (1.0f + Dd) * (1.0f + Dd)
+                               : (1.0f + Dd) * (1.0f + Dd);
+  const float cpsi = fmaf(U, fmaf(168.0f, U, 117.0f), 8.0f);
+  const float r0r = rho0 * rinv * 1.01f;           // rho0 / rho, rounded up
+  const float En = 2.0f * e2u *
+                   (G * (opdD * fmaf(3.0f, cpsi, 52.0f) + 33.0f * r0r) + 8.0f);
+  const float Ex = 1.01f * (6.1f * uu * xabs + En + G * a_extra);
   const DH32 h = series_dh32<L::Q>(M, true, xabs, Ex, rho.hi);
   float alpha = 1.0f;
   const int k = decide32(h, alpha);

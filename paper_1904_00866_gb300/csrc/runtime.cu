@@ -133,7 +133,7 @@ struct elbm_handle {
   unsigned* err_flags = nullptr;
   unsigned* far_count = nullptr;   // [0..1] deferred, [2..3] undecided
   unsigned* far_queue = nullptr;
-  float* refine_buf = nullptr;     // undecided-node buffer [q + 2][cap]
+  float* refine_buf = nullptr;     // undecided-node records [cap][rec]
   unsigned refine_cap = 0;
   unsigned* refine_counts = nullptr;   // per stream-collide block
   int exact = 1;                   // second stage of undecided decisions
@@ -233,8 +233,9 @@ static elbm_status ensure_buffers(elbm_handle* h) {
     // gather path): n / 16 entries, at least 65,536.
     const long long cap =
         std::min<long long>(h->n, std::max<long long>(h->n / 16, 65536));
-    h->refine_buf = (float*)dev_alloc(
-        h, sizeof(float) * (size_t)(h->q + 2) * (size_t)cap);
+    const int rec = h->q == 27 ? refine_record<D3Q27>() : refine_record<D2Q9>();
+    h->refine_buf =
+        (float*)dev_alloc(h, sizeof(float) * (size_t)rec * (size_t)cap);
     h->refine_counts =
         (unsigned*)dev_alloc(h, sizeof(unsigned) * kMaxRefineBlocks);
     h->refine_cap = h->refine_buf && h->refine_counts ? (unsigned)cap : 0u;

@@ -336,17 +336,15 @@ __device__ __forceinline__ bool second_stage32(In in, float rho0f,
   return true;
 }
 
-// Buffer of undecided nodes for the second stage (SoA [Q + 2][cap]: the Q
-// stored values of a node, its key and its provisional alpha), written by
-// the stream-collide kernels and read by the fixup kernel, coalesced both
-// ways; a node that finds the buffer full goes to the deferred-node queue
-// tagged kTagRefine (the fixup then gathers it from f_in).  Every lane of
-// the warp calls; `mine` marks an undecided node, in(i) its stored values,
-// ap its provisional alpha.
-template <class L>
-__host__ __device__ constexpr int refine_rows() {
-  return L::Q + 2;
-}
+// Buffer of undecided nodes for the second stage: one record of
+// refine_record<L>() floats per node (its Q stored values, its key and its
+// provisional alpha, padded to 16 bytes: 128 bytes for D3Q27), written by
+// the stream-collide kernels as whole 16-byte vectors and read by the
+// second-stage kernel; a node that finds its block's segment full goes to
+// the deferred-node queue tagged kTagRefine (the fixup then gathers it
+// from f_in).  Every lane of the warp calls; `mine` marks an undecided
+// node, in(i) its stored values, ap its provisional alpha.
+
 
 // Append the deferred nodes of a warp to the fixup queue with one atomic
 // per warp (every lane of the warp must call; st = kNodeDone for lanes
@@ -405,11 +403,19 @@ __device__ __forceinline__ void defer_undecided(const StepParams& p,
   if (!mine) return;
   const unsigned slot = base + (unsigned)__popc(m & ((1u << lane) - 1u));
   if (slot < seg) {
-    float* b = p.refine_buf + (size_t)blockIdx.x * seg + slot;
+    // one record of refine_record<L>() floats, written as 16-byte vectors
+    float4* rec = reinterpret_cast<float4*>(
+        p.refine_buf +
+        ((size_t)blockIdx.x * seg + slot) * (size_t)refine_record<L>());
+    auto val = [&](int k) {
+      return k < L::Q ? in(k)
+                      : (k == L::Q ? __uint_as_float(node)
+                                   : (k == L::Q + 1 ? ap : 0.0f));
+    };
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) b[(size_t)i * p.refine_cap] = in(i);
-    b[(size_t)L::Q * p.refine_cap] = __uint_as_float(node);
-    b[(size_t)(L::Q + 1) * p.refine_cap] = ap;
+    for (int j = 0; j < refine_record<L>() / 4; ++j)
+      rec[j] = make_float4(val(4 * j), val(4 * j + 1), val(4 * j + 2),
+                           val(4 * j + 3));
   } else {
     const unsigned q = atomicAdd(&p.far_count[p.parity], 1u);
     if (q < p.far_cap)

@@ -51,6 +51,14 @@ struct FastDiv {
 // second stage reads (8 resident blocks on each of up to 256 SMs).
 constexpr int kMaxRefineBlocks = 2048;
 
+// Floats per record of the undecided-node buffer: the Q stored values,
+// the node key and the provisional alpha, padded to whole 16-byte vectors
+// (32 = 128 bytes for D3Q27, 12 for D2Q9).
+template <class L>
+__host__ __device__ constexpr int refine_record() {
+  return (L::Q + 2 + 3) / 4 * 4;
+}
+
 struct StepParams {
   const void* f_in;
   void* f_out;
@@ -79,10 +87,10 @@ struct StepParams {
   const float* in_pop[27];
   float* out_pop[27];
   // Second stage of undecided FP32 decisions (exact: 1; certified: 0, the
-  // certified alpha is final).  Its buffer is SoA [Q + 2][refine_cap]
+  // certified alpha is final).  Its buffer holds refine_cap records
   // (stored values, node key, provisional alpha); block b of a
   // stream-collide launch of G blocks owns the segment of
-  // refine_cap / G entries from b (refine_cap / G) on and writes how many
+  // refine_cap / G records from b (refine_cap / G) on and writes how many
   // it used to refine_counts[b].
   int exact;
   float* refine_buf;

@@ -35,8 +35,8 @@ def request_nodes(req):
 def request_bytes(req):
     """Device bytes a resident run needs: two FP32 population buffers, its
     share of the deferred-node queue (8 B/node, +25 % headroom) and of the
-    undecided-node buffer (29 floats per sixteenth of a node, 8 B/node
-    rounded up), and the transient FP64 field staging of initialisation."""
+    undecided-node buffer (one 128-byte record per sixteen nodes, 8 B/node),
+    and the transient FP64 field staging of initialisation."""
     nodes = request_nodes(req)
     q, d = Q[req["lattice"]], D[req["lattice"]]
     return nodes * (2 * q * 4 + 18 + (1 + d) * 8)
