@@ -16,6 +16,11 @@ relax, store, fused diagnostics on the configured interval).
   roofline     the stream-collide kernel: algorithmic bytes per launch
                (27 x 4 B read + 27 x 4 B written per node) / its average
                CUDA-event duration, against the measured HBM copy peak;
+  decision_modes  the same measurement in both FP32 entropy-decision modes
+               (exact: FP32 decisions not certified are retaken in
+               double-float, FP64 as the last resort -- the default and the
+               headline; certified: those nodes keep an H-safe certified
+               alpha), with each mode's FP64-check decision mismatches;
   secondary    FORMULA vs ROOT and FP32 vs FP64 on 256^3 D3Q27 and on the
                1024^2 D2Q9 double shear layer (not the headline);
   cpu_baseline the CPU FP64 oracle on a bounded sample (64^3 D3Q27 TGV).
@@ -50,9 +55,9 @@ FALLBACK_HBM_GBS = 6800.0
 # while the kernel sources hash to `sha`; scaled to the workload by node
 # count (traffic grows in proportion).
 TRAFFIC_RECORD = {"sha": "595261297a8770a7", "bytes_per_node": 220.7561,
-                  "files": ['fp16_storage.cuh', 'lattice.cuh', 'node_fp32.cuh',
-                            'node_fp64.cuh', 'sc32.cuh', 'stats.cuh',
-                            'stream_collide.cuh']}
+                  "files": ['df32.cuh', 'fp16_storage.cuh', 'lattice.cuh',
+                            'node_fp32.cuh', 'node_fp64.cuh', 'sc32.cuh',
+                            'stats.cuh', 'stream_collide.cuh']}
 
 
 def kernel_sha():
@@ -82,6 +87,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-other-decision", action="store_true",
+                    help="time only --decision, not the other FP32 mode")
     ap.add_argument("--serve-requests", type=int, default=100)
     ap.add_argument("--batch-every", type=int, default=1,
                     help="keep every k-th member of each lattice type of "
@@ -511,6 +518,32 @@ def run_elbm(args):
     g.set_diagnostics(diag_every=1, check_every=1)
     g.step(1, "formula")
     st = g.entropy_stats()
+
+    def mode_entry(ms_, kms_, nk_, st_):
+        kms_ = kms_ / max(nk_, 1)
+        ach = BYTES_PER_LU[("D3Q27", esize)] * nodes / (kms_ * 1e-3) / 1e9
+        return {"value": round(whole_job_mlups(nodes, args.steps, world, ms_),
+                               1),
+                "ms_per_step": round(ms_ / args.steps, 4),
+                "kernel_ms": round(kms_, 4), "frac": round(ach / hbm, 4),
+                "n_band": st_["n_band"], "n_far": st_["n_far"],
+                "n_decision_mismatch": st_["n_decision_mismatch"],
+                "n_violations": st_["n_violations"],
+                "alpha_dev_max": st_["alpha_dev_max"]}
+    # the other FP32 decision mode on the same state, timed the same way
+    other = "certified" if args.decision == "exact" else "exact"
+    modes = {args.decision: mode_entry(ms, kms, nk, st)}
+    if not args.no_other_decision:
+        g.set_decision(other)
+        g.set_diagnostics(diag_every=args.diag_every)
+        g.step(2, "formula")
+        g.sync()
+        barrier(world)
+        ms2, kms2, nk2 = time_steps(g, args.steps, "formula", stream)
+        ms2 = max_over_ranks(ms2, world)
+        g.set_diagnostics(diag_every=1, check_every=1)
+        g.step(1, "formula")
+        modes[other] = mode_entry(ms2, kms2, nk2, g.entropy_stats())
     result = {
         "metric": "MLUPS (D3Q27 FORMULA %s)" % (
             "FP16-shifted" if fp16 else "FP32-shifted"),
@@ -536,7 +569,9 @@ def run_elbm(args):
             "l2": "inputs larger than L2 (%.1f GB of populations read per "
                   "step vs 129 MB L2); no flush" % (nodes * 27 * esize / 1e9),
             "parallelism": "replicas" if world > 1 else "single GPU",
+            "decision": args.decision,
         },
+        "decision_modes": modes,
         "roofline": {
             "bound": "hbm",
             "kernel": ("k_sc16<D3Q27> (pipelined FP16-shifted FORMULA "

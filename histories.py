@@ -48,8 +48,8 @@ def tgv_history(elbm, n, dtype, samples=20, re=1600.0, u0=0.05,
 
     def energy():
         r, v = g.moments()
-        e = 0.5 * float(np.einsum("i...,i...,...->", v, v, r))
-        return e
+        return 0.5 * sum(float(np.vdot(r, v[a] * v[a]))
+                         for a in range(v.shape[0]))
 
     e0, z0 = energy(), g.enstrophy()
     out = {"n": n, "dtype": dtype, "decision": decision, "re": re, "u0": u0,

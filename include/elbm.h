@@ -154,7 +154,10 @@ typedef struct {
   long long n_violations;   /* nodes with Delta H(alpha) above its FP64
                                rounding bound (Eq. (7) violated)          */
   long long n_decision_mismatch; /* FP32 accept/formula decision differs
-                               from the FP64 one                          */
+                               from the FP64 one (nodes where f = f^eq at
+                               the evaluation's precision -- the update
+                               is the identity for every alpha -- are
+                               not compared)                              */
   double alpha_dev_max;     /* max |alpha - alpha_FORMULA in FP64|        */
 } elbm_entropy_stats_t;
 

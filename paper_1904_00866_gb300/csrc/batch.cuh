@@ -397,31 +397,25 @@ __global__ void __launch_bounds__(256) k_batch_refine(const BatchParams bp,
 }
 
 // FP64 fixup of the batch kernel's deferred-node queue (values gathered
-// from the member's buffer): the FP64 FORMULA, after the second stage for
-// entries tagged kTagRefine (a full buffer segment); clears the other
+// from the member's buffer): the second stage for entries tagged
+// kTagRefine (a full buffer segment), one entry per thread, then the FP64
+// FORMULA for the nodes that need it, one node per warp
+// (formula64_warp); entries are dealt as in k_far_fixup.  Clears the other
 // parity's counter for the next step.
 template <int DIAG>
 __global__ void __launch_bounds__(256) k_batch_fixup(const BatchParams bp) {
   const unsigned count = min(bp.far_count[bp.step & 1], bp.far_cap);
-  // entries dealt round-robin over the blocks (see k_far_fixup)
-  for (unsigned k = threadIdx.x * gridDim.x + blockIdx.x; k < count;
-       k += gridDim.x * blockDim.x) {
-    const unsigned long long e = bp.far_queue[k];
-    const int mi = (int)(e >> 32);
-    const unsigned tagged = (unsigned)(e & 0xffffffffu);
-    const unsigned node = tagged & ~kTagRefine;
-    const MemberDesc& m = bp.members[mi];
-    const float* in = pick(m, m.parity0 + bp.step);
-    float* out = pick(m, m.parity0 + bp.step + 1);
-    StepParams g;   // geometry for src_index
-    g.nx = m.nx;
-    g.ny = m.ny;
-    g.nz = m.nz;
-    const int x = (int)(node % (unsigned)m.nx);
-    const int y = (int)((node / (unsigned)m.nx) % (unsigned)m.ny);
-    const int z = (int)(node / ((unsigned)m.nx * (unsigned)m.ny));
-    Acc acc;
-    acc.init();
+  const int lane = threadIdx.x & 31;
+  const unsigned W = gridDim.x * (blockDim.x >> 5);
+  const unsigned wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const LanePop lp27 = lane_pop<D3Q27>(lane), lp9 = lane_pop<D2Q9>(lane);
+  auto coords = [](const MemberDesc& m, unsigned node, int& x, int& y,
+                   int& z) {
+    x = (int)(node % (unsigned)m.nx);
+    y = (int)((node / (unsigned)m.nx) % (unsigned)m.ny);
+    z = (int)(node / ((unsigned)m.nx * (unsigned)m.ny));
+  };
+  auto params = [&](const MemberDesc& m) {
     StepParams pp;
     pp.beta = m.beta64;
     pp.rho0 = m.rho0;
@@ -430,37 +424,133 @@ __global__ void __launch_bounds__(256) k_batch_fixup(const BatchParams bp) {
     pp.alpha_map = m.alpha_map;
     pp.unshifted = 0;
     pp.corr_rho = 0.0f;
-    bool fp64 = false;
-    auto run = [&](auto lat) {
-      using L = decltype(lat);
-      float v[L::Q];
+    return pp;
+  };
+  for (unsigned base = 0; base < count; base += 32u * W) {
+    const unsigned k = base + (unsigned)lane * W + wid;
+    bool need64 = false;
+    unsigned long long e = 0;
+    if (k < count) {
+      e = bp.far_queue[k];
+      const int mi = (int)(e >> 32);
+      const unsigned tagged = (unsigned)(e & 0xffffffffu);
+      const unsigned node = tagged & ~kTagRefine;
+      need64 = true;
+      if (tagged & kTagRefine) {
+        const MemberDesc& m = bp.members[mi];
+        const float* in = pick(m, m.parity0 + bp.step);
+        float* out = pick(m, m.parity0 + bp.step + 1);
+        StepParams g;   // geometry for src_index
+        g.nx = m.nx;
+        g.ny = m.ny;
+        g.nz = m.nz;
+        int x, y, z;
+        coords(m, node, x, y, z);
+        Acc acc;
+        acc.init();
+        const StepParams pp = params(m);
+        auto run = [&](auto lat) {
+          using L = decltype(lat);
+          float v[L::Q];
 #pragma unroll
-      for (int i = 0; i < L::Q; ++i)
-        v[i] = in[(size_t)i * m.n + src_index<L>(g, i, x, y, z)];
-      auto store32 = [&](int i, float val) { out[(size_t)i * m.n + node] = val; };
-      if ((tagged & kTagRefine) &&
-          refine_deferred<L, true, DIAG, 0>(pp, v, node,
-                                            __int_as_float(0x7fc00000), acc,
-                                            store32))
-        return;
-      fp64 = true;
-      Node64<L> nd;
+          for (int i = 0; i < L::Q; ++i)
+            v[i] = in[(size_t)i * m.n + src_index<L>(g, i, x, y, z)];
+          auto store32 = [&](int i, float val) {
+            out[(size_t)i * m.n + node] = val;
+          };
+          return refine_deferred<L, true, DIAG, 0>(
+              pp, v, node, __int_as_float(0x7fc00000), acc, store32);
+        };
+        need64 = !(m.lattice == 1 ? run(D3Q27{}) : run(D2Q9{}));
+        if (DIAG && !need64) member_stats_add(bp, mi, m, acc, false);
+      }
+    }
+    unsigned todo = __ballot_sync(0xffffffffu, need64);
+    if (__popc(todo) > 16) {
+      // many FP64 nodes in this warp's round (the first steps of new
+      // members): one per lane costs less FP64 issue than one per warp
+      if (need64) {
+        const int mi = (int)(e >> 32);
+        const unsigned node = (unsigned)(e & 0xffffffffu) & ~kTagRefine;
+        const MemberDesc& m = bp.members[mi];
+        const float* in = pick(m, m.parity0 + bp.step);
+        float* out = pick(m, m.parity0 + bp.step + 1);
+        StepParams g;   // geometry for src_index
+        g.nx = m.nx;
+        g.ny = m.ny;
+        g.nz = m.nz;
+        int x, y, z;
+        coords(m, node, x, y, z);
+        Acc acc;
+        acc.init();
+        const StepParams pp = params(m);
+        auto run = [&](auto lat) {
+          using L = decltype(lat);
+          Node64<L> nd;
 #pragma unroll
-      for (int i = 0; i < L::Q; ++i) nd.f[i] = L::w(i) * m.rho0 + (double)v[i];
-      auto store = [&](int i, double val) {
-        if (i < 0) {
-          m.alpha_map[node] = (float)val;
-        } else {
-          out[(size_t)i * m.n + node] = (float)(val - L::w(i) * m.rho0);
+          for (int i = 0; i < L::Q; ++i)
+            nd.f[i] = L::w(i) * m.rho0 +
+                      (double)in[(size_t)i * m.n + src_index<L>(g, i, x, y, z)];
+          auto store = [&](int i, double val) {
+            if (i < 0)
+              m.alpha_map[node] = (float)val;
+            else
+              out[(size_t)i * m.n + node] = (float)(val - L::w(i) * m.rho0);
+          };
+          collide64<L, MODE_FORMULA, 0>(nd, pp, true, acc, DIAG != 0, store);
+        };
+        if (m.lattice == 1)
+          run(D3Q27{});
+        else
+          run(D2Q9{});
+        if (DIAG) member_stats_add(bp, mi, m, acc, true);
+      }
+      todo = 0u;
+    }
+    while (todo) {
+      const int src_lane = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const unsigned long long ee = __shfl_sync(0xffffffffu, e, src_lane);
+      const int mi = (int)(ee >> 32);
+      const unsigned node = (unsigned)(ee & 0xffffffffu) & ~kTagRefine;
+      const MemberDesc& m = bp.members[mi];
+      const float* in = pick(m, m.parity0 + bp.step);
+      float* out = pick(m, m.parity0 + bp.step + 1);
+      int x, y, z;
+      coords(m, node, x, y, z);
+      auto run = [&](auto lat, const LanePop& lp) {
+        using L = decltype(lat);
+        double f = 0.0;
+        if (lp.on) {
+          int xs = x - lp.c[0], ys = y - lp.c[1], zs = z - lp.c[2];
+          xs = xs < 0 ? xs + m.nx : (xs >= m.nx ? xs - m.nx : xs);
+          ys = ys < 0 ? ys + m.ny : (ys >= m.ny ? ys - m.ny : ys);
+          zs = zs < 0 ? zs + m.nz : (zs >= m.nz ? zs - m.nz : zs);
+          const size_t src =
+              ((size_t)zs * (size_t)m.ny + (size_t)ys) * (size_t)m.nx +
+              (size_t)xs;
+          f = lp.w * m.rho0 + (double)in[(size_t)lane * m.n + src];
         }
+        return formula64_warp<L>(lp, f, m.beta64, [&](double val) {
+          out[(size_t)lane * m.n + node] = (float)(val - lp.w * m.rho0);
+        });
       };
-      collide64<L, MODE_FORMULA, 0>(nd, pp, true, acc, DIAG != 0, store);
-    };
-    if (m.lattice == 1)
-      run(D3Q27{});
-    else
-      run(D2Q9{});
-    if (DIAG) member_stats_add(bp, mi, m, acc, fp64);
+      const Warp64 r = m.lattice == 1 ? run(D3Q27{}, lp27) : run(D2Q9{}, lp9);
+      if (lane == 0) {
+        if (r.flags & (NF_BAD_NEG | NF_BAD_NONFINITE)) {
+          atomicOr(bp.err_flags, r.flags);
+        } else {
+          if (m.alpha_map) m.alpha_map[node] = (float)r.alpha;
+          if (DIAG) {
+            Acc acc;
+            acc.init();
+            acc.add_moments(r.rho - m.rho0, r.j, r.rho);
+            acc.add_alpha(r.alpha, r.flags, 0);
+            member_stats_add(bp, mi, m, acc, true);
+          }
+        }
+      }
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) bp.far_count[(bp.step & 1) ^ 1] = 0u;
 }

@@ -7,12 +7,14 @@
 //     much smaller error bound (node32_refine), and the populations the
 //     decided alpha changes rewritten.
 //   k_far_fixup: the FP64 FORMULA (Eqs. (8)-(9) with logarithms, alpha
-//     rounded down to FP32) for nodes far from equilibrium (max |x_i| > 1/8,
-//     |u| >= 1/2), invalid states and the rare node the second stage left
-//     undecided.  It also resets the other parity's counter for the next
-//     step (stream order makes that counter idle here).
+//     rounded down to FP32; one node per warp) for nodes far from
+//     equilibrium (max |x_i| > 1/8, a velocity component >= 1/4), invalid
+//     states and the rare node the second stage left undecided.  It also
+//     resets the other parity's counter for the next step (stream order
+//     makes that counter idle here).
 #pragma once
 #include "sc32.cuh"
+#include "warp64.cuh"
 
 namespace elbm {
 
@@ -38,7 +40,7 @@ __device__ __forceinline__ bool refine_deferred(const StepParams& p,
           Node64<L> nd;
           const Check64 ck = check32<L, SHIFTED>(in, p.rho0, r.alpha, nd);
           acc.add_check(ck.h, ck.violation,
-                        ((r.flags & NF_ACCEPT_STAR) != 0) != ck.accept_ref,
+                        decision_mismatch(r.flags, ck.accept_ref),
                         fabs((double)r.alpha - ck.alpha_ref));
         }
       });
@@ -125,73 +127,150 @@ __global__ void __launch_bounds__(256, 2) k_refine_stage(const StepParams p,
 
 // FP64 fixup (S: the storage type, float or half_t): the deferred-node
 // queue, with values gathered from f_in.  Entries tagged kTagRefine (a
-// full buffer segment, or no buffer) take the second stage here first.
+// full buffer segment, or no buffer) take the second stage here first, one
+// entry per thread; the nodes that need the FP64 FORMULA are then collided
+// one at a time by their whole warp (formula64_warp, one population per
+// lane).  Lane l of warp w takes entry w + l W of each round of 32 W
+// entries (W warps in the grid), so a short queue leaves at most a few
+// FP64 nodes to each warp and a long one (the first step after
+// initialisation) still gives every lane its own entry; a warp with more
+// than 16 FP64 nodes in a round runs them one per lane.  On steps with the
+// FP64 entropy check (CHECK) the FP64 nodes run on their own lanes, as the
+// check's statistics need each node's populations in one thread.
 template <class L, class S, int DIAG, int CHECK>
 __global__ void __launch_bounds__(256) k_far_fixup(const StepParams p) {
   constexpr int Q = L::Q;
   const unsigned count = min(p.far_count[p.parity], p.far_cap);
   const bool shifted = sizeof(S) == 2 || !p.unshifted;
+  const int lane = threadIdx.x & 31;
+  const unsigned W = gridDim.x * (blockDim.x >> 5);
+  const unsigned wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const LanePop lp = lane_pop<L>(lane);
   Acc acc;
   acc.init();
-  // entries dealt round-robin over the blocks: a short queue of FP64 nodes
-  // (each ~1,500 FP64 instructions) spreads over every SM instead of
-  // filling the first few
-  for (unsigned k = threadIdx.x * gridDim.x + blockIdx.x; k < count;
-       k += gridDim.x * blockDim.x) {
-    const unsigned e = p.far_queue[k];
-    const long long node = e & ~kTagRefine;
-    const int x = (int)(node % p.nx);
-    const int y = (int)((node / p.nx) % p.ny);
-    const int z = (int)(node / ((long long)p.nx * p.ny));
-    float v[Q];
+  auto coords = [&](long long node, int& x, int& y, int& z) {
+    x = (int)(node % p.nx);
+    y = (int)((node / p.nx) % p.ny);
+    z = (int)(node / ((long long)p.nx * p.ny));
+  };
+  auto out_s = [&](long long node, int i, float val) {
+    if constexpr (sizeof(S) == 2)
+      reinterpret_cast<unsigned short*>(p.out_pop[i])[node] =
+          h16_bits<L>(val, i);
+    else
+      p.out_pop[i][node] = val;
+  };
+  for (unsigned base = 0; base < count; base += 32u * W) {
+    const unsigned k = base + (unsigned)lane * W + wid;
+    bool need64 = false;
+    long long node = 0;
+    if (k < count) {
+      const unsigned e = p.far_queue[k];
+      node = e & ~kTagRefine;
+      need64 = true;
+      if (e & kTagRefine) {
+        int x, y, z;
+        coords(node, x, y, z);
+        float v[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const long long src = src_index<L>(p, i, x, y, z);
-      if constexpr (sizeof(S) == 2)
-        v[i] = h16_dev<L>(reinterpret_cast<const unsigned short*>(
+        for (int i = 0; i < Q; ++i) {
+          const long long src = src_index<L>(p, i, x, y, z);
+          if constexpr (sizeof(S) == 2)
+            v[i] = h16_dev<L>(reinterpret_cast<const unsigned short*>(
+                                  p.in_pop[i])[src],
+                              i);
+          else
+            v[i] = p.in_pop[i][src];
+        }
+        const float ap = __int_as_float(0x7fc00000);   // NaN: recomputed
+        auto out = [&](int i, float val) { out_s(node, i, val); };
+        need64 = !(shifted ? refine_deferred<L, true, DIAG, CHECK>(
+                                 p, v, node, ap, acc, out)
+                           : refine_deferred<L, false, DIAG, CHECK>(
+                                 p, v, node, ap, acc, out));
+      }
+    }
+    // FP64 nodes of this round: with many of them in the warp (the first
+    // step after initialisation) one per lane costs less FP64 issue than
+    // one per warp; with few (developed flows) one per warp ends sooner.
+    // The check's statistics need each node in one thread.
+    const unsigned m64 = __ballot_sync(0xffffffffu, need64);
+    if (CHECK != 0 || __popc(m64) > 16) {
+      if (!need64) continue;
+      int x, y, z;
+      coords(node, x, y, z);
+      Node64<L> nd;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const long long src = src_index<L>(p, i, x, y, z);
+        double vi;
+        if constexpr (sizeof(S) == 2)
+          vi = h16_dev<L>(reinterpret_cast<const unsigned short*>(
                               p.in_pop[i])[src],
                           i);
-      else
-        v[i] = p.in_pop[i][src];
-    }
-    if (e & kTagRefine) {
-      const float ap = __int_as_float(0x7fc00000);   // NaN: recomputed
-      bool done;
-      if constexpr (sizeof(S) == 2) {
-        done = refine_deferred<L, true, DIAG, CHECK>(
-            p, v, node, ap, acc, [&](int i, float val) {
-              reinterpret_cast<unsigned short*>(p.out_pop[i])[node] =
-                  h16_bits<L>(val, i);
-            });
-      } else {
-        auto out = [&](int i, float val) { p.out_pop[i][node] = val; };
-        done = shifted ? refine_deferred<L, true, DIAG, CHECK>(p, v, node, ap,
-                                                               acc, out)
-                       : refine_deferred<L, false, DIAG, CHECK>(p, v, node, ap,
-                                                                acc, out);
+        else
+          vi = p.in_pop[i][src];
+        nd.f[i] = shifted ? L::w(i) * p.rho0 + vi : vi;
       }
-      if (done) continue;
-    }
-    // FP64 FORMULA from the stored values
-    Node64<L> nd;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const double vi = (double)v[i];
-      nd.f[i] = shifted ? L::w(i) * p.rho0 + vi : vi;
-    }
-    auto store_s = [&](int i, double val) {
-      if (i < 0) {
-        p.alpha_map[node] = (float)val;
-      } else if constexpr (sizeof(S) == 2) {
-        reinterpret_cast<half_t*>(p.out_pop[i])[node] =
-            h16_from_dev<L>(val - L::w(i) * p.rho0, i);
-      } else {
-        p.out_pop[i][node] =
-            (float)(p.unshifted ? val : val - L::w(i) * p.rho0);
+      auto store_s = [&](int i, double val) {
+        if (i < 0) {
+          p.alpha_map[node] = (float)val;
+        } else if constexpr (sizeof(S) == 2) {
+          reinterpret_cast<half_t*>(p.out_pop[i])[node] =
+              h16_from_dev<L>(val - L::w(i) * p.rho0, i);
+        } else {
+          p.out_pop[i][node] =
+              (float)(p.unshifted ? val : val - L::w(i) * p.rho0);
+        }
+      };
+      if (DIAG) acc.far += 1;
+      collide64<L, MODE_FORMULA, CHECK>(nd, p, true, acc, DIAG != 0, store_s);
+    } else {
+      unsigned m = m64;
+      while (m) {
+        const int src_lane = __ffs(m) - 1;
+        m &= m - 1;
+        const long long nd = __shfl_sync(0xffffffffu, node, src_lane);
+        int x, y, z;
+        coords(nd, x, y, z);
+        double f = 0.0;
+        if (lp.on) {
+          int xs = x - lp.c[0], ys = y - lp.c[1], zs = z - lp.c[2];
+          xs = xs < 0 ? xs + p.nx : (xs >= p.nx ? xs - p.nx : xs);
+          ys = ys < 0 ? ys + p.ny : (ys >= p.ny ? ys - p.ny : ys);
+          zs = zs < 0 ? zs + p.nz : (zs >= p.nz ? zs - p.nz : zs);
+          const long long src = ((long long)zs * p.ny + ys) * p.nx + xs;
+          if constexpr (sizeof(S) == 2) {
+            const unsigned short b =
+                reinterpret_cast<const unsigned short*>(p.in_pop[lane])[src];
+            f = (double)(__half2float(__ushort_as_half(b)) * lp.hscale_inv);
+          } else {
+            f = (double)p.in_pop[lane][src];
+          }
+          if (shifted) f += lp.w * p.rho0;
+        }
+        const Warp64 r = formula64_warp<L>(lp, f, p.beta, [&](double val) {
+          if constexpr (sizeof(S) == 2)
+            reinterpret_cast<half_t*>(p.out_pop[lane])[nd] =
+                __double2half((val - lp.w * p.rho0) * (double)lp.hscale);
+          else
+            p.out_pop[lane][nd] =
+                (float)(p.unshifted ? val : val - lp.w * p.rho0);
+        });
+        if (lane == 0) {
+          if (DIAG) acc.far += 1;
+          if (r.flags & (NF_BAD_NEG | NF_BAD_NONFINITE)) {
+            atomicOr(p.err_flags, r.flags);
+          } else {
+            if (p.alpha_map) p.alpha_map[nd] = (float)r.alpha;
+            if (DIAG) {
+              acc.add_moments(r.rho - p.rho0, r.j, r.rho);
+              acc.add_alpha(r.alpha, r.flags, 0);
+            }
+          }
+        }
       }
-    };
-    if (DIAG) acc.far += 1;
-    collide64<L, MODE_FORMULA, CHECK>(nd, p, true, acc, DIAG != 0, store_s);
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) p.far_count[p.parity ^ 1] = 0u;
   if (DIAG) acc.block_reduce_store(p.partials);

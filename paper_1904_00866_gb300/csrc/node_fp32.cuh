@@ -30,7 +30,9 @@
 //                                      chord root decreases in both values,
 //                                      so it stays at or below the exact
 //                                      Eq. (9) value, which is at or below
-//                                      the root of Eq. (4));
+//                                      the root of Eq. (4)); in the exact
+//                                      mode only when the bounds fix the
+//                                      chord to within 2^-16;
 //   otherwise (a sign within the FP32 error, or n zero in FP32)
 //                                   -> second stage: n_i recomputed in
 //                                      double-float arithmetic and the same
@@ -95,6 +97,16 @@ struct N32 {
 };
 
 __host__ __device__ constexpr int cidx(int c) { return c + 1; }
+
+// Largest velocity component the FP32 paths take.  Their error bounds use
+// 1 - Dd, Dd = 3U + 3U^2 >= |d_a|, as a lower bound of every equilibrium
+// factor 1 + d_a; that bound is positive only for U < 0.264, so nodes with
+// a larger component go to the FP64 fixup.
+constexpr float kUMax32 = 0.25f;
+
+// Largest uncertainty of an Eq. (9) chord the exact decision mode accepts
+// from an evaluation's bounds (2^-16); a wider one goes to the next stage.
+constexpr float kChordWidth = 1.52587890625e-05f;
 
 // 1 / y by the SFU (rcp.approx.ftz.f32, relative error below 2^-23).
 // The other approximate operations below are used with their documented
@@ -212,16 +224,22 @@ __device__ __forceinline__ DH32 series_dh32(const float (&M)[9], bool k8,
 }
 
 // The FP32 decision between the acceptance of alpha = 2 (after Eq. (8)) and
-// the chord of Eq. (9), each taken only when certified by the bounds.
+// the chord of Eq. (9), each taken only when certified by the bounds.  A
+// chord whose value the bounds leave uncertain by more than wmax (the
+// chord on the lower bounds minus the chord on the upper bounds) is left
+// undecided too, so that the exact mode's alpha stays within wmax of the
+// Eq. (9) value of the exact state (pass INFINITY to accept any width).
 enum { kAcceptTwo = 0, kChord = 1, kUndecided = 2 };
-__device__ __forceinline__ int decide32(const DH32& h, float& alpha) {
+__device__ __forceinline__ int decide32(const DH32& h, float& alpha,
+                                        float wmax) {
   const float D2hi = __fadd_ru(h.D2, h.e2);
   if (D2hi <= 0.0f) {
     alpha = 2.0f;
     return kAcceptTwo;
   }
   const float D1hi = __fadd_ru(h.D1, h.e1);
-  if (!(__fsub_rd(h.D2, h.e2) > 0.0f) || !(D1hi < 0.0f)) return kUndecided;
+  const float D2lo = __fsub_rd(h.D2, h.e2);
+  if (!(D2lo > 0.0f) || !(D1hi < 0.0f)) return kUndecided;
   // alpha = 2 + D2hi / (D2hi - D1hi) (1 - 2), rounded down: the chord root
   // decreases in both values, so it stays at or below the exact Eq. (9)
   // value.  t = D2hi / (D2hi - D1hi) rounded up: the approximate quotient
@@ -229,6 +247,14 @@ __device__ __forceinline__ int decide32(const DH32& h, float& alpha) {
   const float den = __fsub_rd(D2hi, D1hi);
   const float tt = __fmul_ru(__fdividef(D2hi, den), 1.0f + 2.384185791e-7f);
   alpha = __fsub_rd(2.0f, tt);
+  if (wmax < INFINITY) {
+    // the chord on the lower bounds, t rounded down: the exact Eq. (9)
+    // value lies in [alpha, 2 - tlo]
+    const float tlo =
+        __fmul_rd(__fdividef(D2lo, __fsub_ru(D2lo, __fsub_rd(h.D1, h.e1))),
+                  1.0f - 2.384185791e-7f);
+    if (!(tt - tlo <= wmax)) return kUndecided;
+  }
   return kChord;
 }
 
@@ -354,7 +380,7 @@ __device__ __forceinline__ void node32_refine(
     psi[a][0] = df_add(df_add(df_neg(u3), s2), 1.0f);   // 1 - 3u + 2s
     psi[a][1] = df_add(df_neg(sv), 1.0f);               // 1 - s
   }
-  if (!(U < 0.5f)) {
+  if (!(U < kUMax32)) {
     r.flags = NF_FAR;
     return;
   }
@@ -438,7 +464,7 @@ __device__ __forceinline__ void node32_refine(
   }
   // Error of x_i: the rounding of n_i to FP32, of f_i and of the quotient
   // (6.1 u |x_i|) plus the double-float error of n_i divided by
-  // f_i >= W_i rho / G.  With e = u^2 and |u_a| <= U < 1/2: u within
+  // f_i >= W_i rho / G.  With e = u^2 and |u_a| <= U < 1/4: u within
   // 23 e U (corrected quotient), s within 40 e s <= 60 e U^2 (one Newton
   // step from a 9.5 u value), d = +-3u + 2s within 93 e U + 144 e U^2 (with
   // its sum's rounding), 1 + d within c e, c = 8 + 117 U + 168 U^2; the
@@ -461,7 +487,7 @@ __device__ __forceinline__ void node32_refine(
   const float Ex = 1.01f * (6.1f * uu * xabs + En + G * a_extra);
   const DH32 h = series_dh32<L::Q>(M, true, xabs, Ex, rho.hi);
   float alpha = 1.0f;
-  const int k = decide32(h, alpha);
+  const int k = decide32(h, alpha, kChordWidth);
   if (k == kUndecided) {
     r.flags = NF_FAR;
     return;
@@ -528,7 +554,7 @@ __device__ __forceinline__ void node32_formula(
     dm[a] = fmaf(-3.0f, u, 2.0f * s);
     dz[a] = -s;
   }
-  if (!(U < 0.5f)) {
+  if (!(U < kUMax32)) {
     r.flags = NF_FAR;
     return;
   }
@@ -560,7 +586,7 @@ __device__ __forceinline__ void node32_formula(
     wd[k] = wk * drho;
     w0[k] = wk * rho0;
   }
-  float M2, M3, M4, xabs;
+  float M2, M3, M4, xabs, gmax;
   {   // rest population
     float pm1 = pxy[1][1].x;
     if (L::D == 3) pm1 = fmaf(pm1, dz[2], pm1 + dz[2]);
@@ -568,8 +594,10 @@ __device__ __forceinline__ void node32_formula(
     if (!SHIFTED) deq += corr[0];
     const float ni = deq - d0;
     r.n0 = ni;
-    const float x = ni * rcp_approx(w0[0] + d0);
+    const float rf = rcp_approx(w0[0] + d0);
+    const float x = ni * rf;
     xabs = fabsf(x);
+    gmax = wr[0] * rf;                         // W rho / f
     M2 = ni * x;                               // f x^2
     M3 = M2 * x;                               // f x^3
     M4 = M3 * x;                               // f x^4
@@ -589,8 +617,11 @@ __device__ __forceinline__ void node32_formula(
     if (!SHIFTED) deq = add2(deq, make_float2(corr[i], corr[i + 1]));
     const float2 ni = sub2(deq, dd[k]);
     r.n2[k] = ni;
-    const float2 x = mul2(ni, rcp_approx2(add2(f2(w0[kc]), dd[k])));
+    const float2 rf = rcp_approx2(add2(f2(w0[kc]), dd[k]));
+    const float2 x = mul2(ni, rf);
     xabs = fmaxf(xabs, fmaxf(fabsf(x.x), fabsf(x.y)));
+    const float2 gw = mul2(f2(wr[kc]), rf);
+    gmax = fmaxf(gmax, fmaxf(gw.x, gw.y));
     const float2 q1 = mul2(ni, x);
     const float2 q2 = mul2(q1, x);
     if (k == 0) {
@@ -669,14 +700,25 @@ __device__ __forceinline__ void node32_formula(
   // upper bound of a positive quotient: the 2-ulp approximate division
   // raised by 2^-20 (covers its error and the product's rounding)
   constexpr float kUp = 1.00000095367431640625f;   // 1 + 2^-20
-  const float G = __fdividef(1.0f + xabs, omdD) * kUp;
+  // G >= max_i W_i rho / f_i: the a-priori bound (1 + xabs) / (1 - Dd)^D,
+  // or the node's own maximum gmax of W_i rho fl(1 / fl(W_i rho0 + delta_i))
+  // when smaller.  gmax kUp covers the reciprocal's and the products'
+  // rounding; the sum fl(W_i rho0 + delta_i) is within u (W_i rho0 + f_i)
+  // of f_i, which the division by 1 - u - u gmax kUp rho0 / rho covers
+  // (the denominator stays above 1/2 whenever the result is used).
+  const float Gb = __fdividef(1.0f + xabs, omdD) * kUp;
+  const float gk = gmax * kUp;
+  const float den =
+      1.0f - uu - uu * gk * (rho0 * inv_rho * 1.01f);
+  const float G =
+      den > 0.5f ? fminf(Gb, __fdividef(gk, den) * kUp) : Gb;
   const float Ex =
       1.05f * (G * (EP + 3.0f * uu * (fabsf(drho) * inv_rho + 3.0f * Dd) +
                     2e-11f * inv_rho + a_extra) +
                6.0f * uu * xabs);
   const DH32 h = series_dh32<Q>(M, k8, xabs, Ex, rho);
   float alpha = 2.0f;
-  const int k = decide32(h, alpha);
+  const int k = decide32(h, alpha, exact ? kChordWidth : INFINITY);
   if (k == kUndecided) {
     // The sign of Delta H(2) or of Delta H(1) is within the FP32 error.
     // Without a second stage (exact false) the node takes the certified

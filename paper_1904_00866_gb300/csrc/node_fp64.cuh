@@ -241,6 +241,17 @@ __device__ __forceinline__ double node64_alpha(const Node64<L>& s,
   return alpha_formula64(s, flags);
 }
 
+// Whether a node's branch (acceptance of alpha_* or Eq. (9)) differs from
+// the FP64 check's.  Nodes whose evaluation found f^eq = f to its working
+// precision (NF_DEGENERATE: n = 0, so f*(alpha) = f for every alpha) have no
+// branch to compare: the FP64 evaluation of the same node decides by its
+// own rounding noise there.
+__device__ __forceinline__ bool decision_mismatch(unsigned flags,
+                                                  bool accept_ref) {
+  return (flags & NF_DEGENERATE) == 0u &&
+         ((flags & NF_ACCEPT_STAR) != 0) != accept_ref;
+}
+
 // FP64 check of one node at the alpha actually used: Delta H(alpha) against
 // its rounding bound (the Eq. (7) violation test), the entropy H(f) of
 // Eq. (3), and the FP64 FORMULA alpha for comparison.

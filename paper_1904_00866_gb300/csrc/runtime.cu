@@ -228,11 +228,16 @@ static elbm_status ensure_buffers(elbm_handle* h) {
   h->far_count = (unsigned*)dev_alloc(h, 256);
   if (h->dtype != ELBM_FP64) {
     h->far_queue = (unsigned*)dev_alloc(h, sizeof(unsigned) * h->n);
-    // Undecided nodes of a step (about 1-3 % on developed flows; nearly all
-    // on the first step after initialisation, where the overflow takes the
-    // gather path): n / 16 entries, at least 65,536.
+    // Undecided nodes of a step: about 1-3 % of a developed 3D flow, but
+    // most nodes of a flow whose non-equilibrium part is near FP32
+    // resolution (a thin shear layer at Re 30,000) and of the first step
+    // after initialisation; a full buffer sends the rest to the gathering
+    // queue.  D2Q9: every node (48-byte records); D3Q27: n / 16 entries
+    // (8 B per node), at least 65,536.
     const long long cap =
-        std::min<long long>(h->n, std::max<long long>(h->n / 16, 65536));
+        h->q == 9 ? h->n
+                  : std::min<long long>(h->n,
+                                        std::max<long long>(h->n / 16, 65536));
     const int rec = h->q == 27 ? refine_record<D3Q27>() : refine_record<D2Q9>();
     h->refine_buf =
         (float*)dev_alloc(h, sizeof(float) * (size_t)rec * (size_t)cap);

@@ -255,7 +255,7 @@ __device__ __forceinline__ void diag32(const N32<L>& r, In in, double rho0,
     const Check64 ck = check32<L, SHIFTED>(in, rho0, r.alpha, nd);
     acc.h += ck.h;
     acc.viol += ck.violation;
-    acc.mismatch += ((r.flags & NF_ACCEPT_STAR) != 0) != ck.accept_ref;
+    acc.mismatch += decision_mismatch(r.flags, ck.accept_ref);
     acc.adev = fmax(acc.adev, fabs((double)r.alpha - ck.alpha_ref));
   }
 }
@@ -400,29 +400,31 @@ __device__ __forceinline__ void defer_undecided(const StepParams& p,
   unsigned base = 0u;
   if (lane == leader) base = atomicAdd(block_count, (unsigned)__popc(m));
   base = __shfl_sync(0xffffffffu, base, leader);
-  if (!mine) return;
-  const unsigned slot = base + (unsigned)__popc(m & ((1u << lane) - 1u));
-  if (slot < seg) {
-    // one record of refine_record<L>() floats, written as 16-byte vectors
-    float4* rec = reinterpret_cast<float4*>(
-        p.refine_buf +
-        ((size_t)blockIdx.x * seg + slot) * (size_t)refine_record<L>());
-    auto val = [&](int k) {
-      return k < L::Q ? in(k)
-                      : (k == L::Q ? __uint_as_float(node)
-                                   : (k == L::Q + 1 ? ap : 0.0f));
-    };
+  bool over = false;
+  if (mine) {
+    const unsigned slot = base + (unsigned)__popc(m & ((1u << lane) - 1u));
+    if (slot < seg) {
+      // one record of refine_record<L>() floats, written as 16-byte vectors
+      float4* rec = reinterpret_cast<float4*>(
+          p.refine_buf +
+          ((size_t)blockIdx.x * seg + slot) * (size_t)refine_record<L>());
+      auto val = [&](int k) {
+        return k < L::Q ? in(k)
+                        : (k == L::Q ? __uint_as_float(node)
+                                     : (k == L::Q + 1 ? ap : 0.0f));
+      };
 #pragma unroll
-    for (int j = 0; j < refine_record<L>() / 4; ++j)
-      rec[j] = make_float4(val(4 * j), val(4 * j + 1), val(4 * j + 2),
-                           val(4 * j + 3));
-  } else {
-    const unsigned q = atomicAdd(&p.far_count[p.parity], 1u);
-    if (q < p.far_cap)
-      p.far_queue[q] = node | kTagRefine;
-    else
-      atomicOr(p.err_flags, NF_BAD_NONFINITE);   // cannot happen: cap = n
+      for (int j = 0; j < refine_record<L>() / 4; ++j)
+        rec[j] = make_float4(val(4 * j), val(4 * j + 1), val(4 * j + 2),
+                             val(4 * j + 3));
+    } else {
+      over = true;
+    }
   }
+  // a full segment: the tagged queue (one atomic per warp; after
+  // initialisation nearly every node of the first step lands here)
+  defer_nodes(&p.far_count[p.parity], p.far_queue, p.far_cap, p.err_flags,
+              node, over ? kNodeRefine : kNodeDone);
 }
 
 // Block prologue / epilogue of the buffer: the block's entry counter in

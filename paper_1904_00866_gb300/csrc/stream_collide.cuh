@@ -146,7 +146,7 @@ __device__ __forceinline__ void collide64(Node64<L>& nd, const StepParams& p,
     if (CHECK) {
       Check64 ck = node64_check(nd, alpha);
       acc.add_check(ck.h, ck.violation,
-                    ((flags & NF_ACCEPT_STAR) != 0) != ck.accept_ref,
+                    decision_mismatch(flags, ck.accept_ref),
                     fabs(alpha - ck.alpha_ref));
     }
   }

@@ -114,6 +114,46 @@ def test_batch_one_step_vs_oracle(elbm, orc, graphs):
     b.close()
 
 
+def test_batch_far_nodes_vs_oracle(elbm, orc):
+    """Members whose flow is rough at the grid scale (modes |k| <= 8 at
+    max |u| = 0.3) leave nodes far from equilibrium after a step; the
+    batch fixup collides them in FP64, one node per warp.  One step from
+    the same stored state against the oracle: populations within
+    2e-6 max(|f_i|, W_i rho0) (at velocities near 1/4 some f_i lie far below
+    W_i rho0, and FP32 forms f^eq_i - f_i to a fixed fraction of W_i rho),
+    the FP64 FORMULA's branch at every node, alpha within 2e-5."""
+    b = elbm.Batch(burst=1, use_graphs=False, autotune=False, diag_every=1)
+    specs = [("D2Q9", (1, 30, 26), 2e-3, 51), ("D3Q27", (10, 9, 12), 2e-3, 52)]
+    ids = []
+    for lat, (nz, ny, nx), nu, seed in specs:
+        if lat == "D2Q9":
+            rho, u = W.random_phase_2d(nx, seed, umax=0.3, ny=ny, kmax=8)
+        else:
+            rho, u = W.random_phase_3d(nx, seed, umax=0.3, ny=ny, nz=nz,
+                                       kmax=4)
+        ids.append(b.add(lat, nx, ny, nz, nu, rho, u))
+    for mid in ids:
+        b.record_alpha(mid)
+    b.step(1)
+    f_pre = {mid: b.populations(mid) for mid in ids}
+    b.step(1)
+    for mid, (lat, (nz, ny, nx), nu, _) in zip(ids, specs):
+        s = b.entropy_stats(mid)
+        assert s["n_far"] > 0, (lat, s["n_far"])
+        o = orc.Lattice(lat, nx, ny, nz, nu=nu)
+        o.set_populations(f_pre[mid])
+        amaps, _ = o.step(1, alpha_map=True, stats=True)
+        f = b.populations(mid)
+        _, w = orc.lattice(lat)
+        wr = w.reshape((-1,) + (1,) * 3)
+        err = np.abs(f - o.f) / np.maximum(np.abs(o.f), wr)
+        assert err.max() <= POP_TOL, (lat, err.max())
+        ag = b.alpha_map(mid).astype(np.float64)
+        assert np.all((amaps[0] == 2.0) == (ag == 2.0))
+        assert np.abs(ag - amaps[0]).max() < 2e-5
+    b.close()
+
+
 @pytest.mark.parametrize("graphs", [True, False])
 def test_batch_members_and_late_joiner_track_oracle(elbm, orc, graphs):
     b = elbm.Batch(burst=8, use_graphs=graphs, autotune=True)

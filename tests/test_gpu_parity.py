@@ -253,6 +253,63 @@ def test_fp32_single_step_alpha_against_fp64(elbm, orc, lat, shape, nu,
     assert np.all(np.abs(f - o.f) <= 2e-6 * np.abs(o.f))
 
 
+@pytest.mark.parametrize("dtype", ["fp32_shifted", "fp16_shifted"])
+@pytest.mark.parametrize("init", ["noise", "rough"])
+@pytest.mark.parametrize("lat,shape", [("D2Q9", (1, 40, 36)),
+                                       ("D3Q27", (8, 10, 12))])
+def test_fp64_fixup_of_far_nodes_vs_oracle(elbm, orc, lat, shape, init,
+                                           dtype):
+    """Nodes far from equilibrium leave the FP32 kernels for the FP64
+    fixup, which collides each node with a whole warp (one population per
+    lane): populations multiplied by 1 + 0.3 U(-1, 1) ("noise"), or a flow
+    rough at the grid scale with velocities up to 0.3 after a step
+    ("rough": the components above 1/4 are the FP32 paths' velocity limit).
+    One step without the FP64 check (the check's steps take the per-thread
+    path) against the oracle's step of the same stored state: the FP64
+    FORMULA's branch at every node, alpha within 2e-5 (the FP64 nodes' alpha
+    rounded down to FP32; the FP32 nodes' Eq. (9) chord within its 2^-16
+    certified width), populations within the FP32 arithmetic in units of
+    W_i rho0 (2e-6 max(|f_i|, W_i rho0): at velocities near 1/4 some f_i
+    lie far below W_i rho0, and FP32 forms f^eq_i - f_i to a fixed fraction
+    of W_i rho) plus, for binary16 storage, 2^-10 of the stored deviation
+    f - W rho0."""
+    nz, ny, nx = shape
+    um, km = (0.05, 4) if init == "noise" else (0.3, 8 if lat == "D2Q9" else 4)
+    if lat == "D2Q9":
+        rho, u = W.random_phase_2d(nx, 5, umax=um, ny=ny, kmax=km)
+    else:
+        rho, u = W.random_phase_3d(nx, 5, umax=um, ny=ny, nz=nz, kmax=km)
+    nu = 2e-4
+    g = elbm.Lattice(lat, nx, ny, nz, nu=nu, dtype=dtype)
+    g.init_fields(rho, u)
+    if init == "noise":
+        f = g.populations()
+        rng = np.random.default_rng(8)
+        g.set_populations(f * (1.0 + 0.3 * rng.uniform(-1.0, 1.0, f.shape)))
+    else:
+        g.step(1, "formula")
+    loaded = g.populations()
+    g.set_diagnostics(diag_every=1, alpha_map_every=1)
+    o = orc.Lattice(lat, nx, ny, nz, nu=nu)
+    o.set_populations(loaded)
+    amaps, _ = o.step(1, alpha_map=True, stats=True)
+    g.step(1, "formula")
+    s = g.entropy_stats()
+    assert s["n_far"] > (0.2 * s["n_nodes"] if init == "noise" else 0), \
+        s["n_far"]
+    ag = g.alpha_map().astype(np.float64)
+    ao = amaps[0]
+    assert np.all((ao == 2.0) == (ag == 2.0))
+    assert np.abs(ag - ao).max() < 2e-5
+    fg = g.populations()
+    _, w = orc.lattice(lat)
+    wr = w.reshape((-1,) + (1,) * 3) * g.rho0
+    tol = 2e-6 * np.maximum(np.abs(o.f), wr)
+    if dtype == "fp16_shifted":
+        tol += 2.0 ** -10 * np.abs(o.f - wr)
+    assert np.all(np.abs(fg - o.f) <= tol), np.max(np.abs(fg - o.f) / tol)
+
+
 def test_fp32_random_phase_zero_violations(elbm):
     n = 32
     rho, u = W.random_phase_3d(n, seed=2, umax=0.05)
