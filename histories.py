@@ -9,9 +9,10 @@ t_c = L / u0 (rounded to whole steps); after every t_c the run records
 the kinetic energy 1/2 sum rho |u|^2 (from the moments) and the enstrophy
 1/2 <|curl u|^2> (central differences, computed on the device), both
 divided by their initial values so that runs at different resolutions are
-comparable, and the entropy statistics of that step (the FP64 check's
+comparable, and the entropy statistics of the diagnostic step of the
+interval (its first step: 0, t_c, 2 t_c, ...): the FP64 check's
 H-increase and decision-mismatch counts, the share of nodes on Eq. (9),
-the smallest alpha).
+the smallest alpha.
 
     python histories.py run --n 256 --dtype fp64 --tc 20 --out a.json
     python histories.py run --n 256 --dtype fp32_shifted --out b.json
@@ -56,7 +57,7 @@ def tgv_history(elbm, n, dtype, samples=20, re=1600.0, u0=0.05,
            "nu": nu, "tc_steps": tc, "e0": e0, "z0": z0,
            "t": [], "energy": [], "enstrophy": [], "n_violations": [],
            "n_decision_mismatch": [], "share_eq9": [], "alpha_min": [],
-           "seconds": []}
+           "stats_step": [], "seconds": []}
     for k in range(1, samples + 1):
         t0 = time.time()
         g.step(tc, "formula")
@@ -70,6 +71,7 @@ def tgv_history(elbm, n, dtype, samples=20, re=1600.0, u0=0.05,
         out["n_decision_mismatch"].append(int(s["n_decision_mismatch"]))
         out["share_eq9"].append(float(s["n_formula"]) / float(n) ** 3)
         out["alpha_min"].append(float(s["alpha_min"]))
+        out["stats_step"].append(int(s["step"]))
         out["seconds"].append(round(dt, 3))
         if out_path:
             with open(out_path, "w") as f:

@@ -330,14 +330,7 @@ template <int DIAG>
 __global__ void __launch_bounds__(256) k_batch_refine(const BatchParams bp,
                                                       int blocks) {
   __shared__ unsigned pre[kMaxRefineBlocks + 1];
-  for (int b = threadIdx.x; b < blocks; b += blockDim.x)
-    pre[b + 1] = bp.refine_counts[b];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    pre[0] = 0u;
-    for (int b = 1; b <= blocks; ++b) pre[b] += pre[b - 1];
-  }
-  __syncthreads();
+  block_prefix(bp.refine_counts, blocks, pre);
   const unsigned total = pre[blocks];
   const unsigned seg = bp.refine_cap / (unsigned)blocks;
   for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < total;

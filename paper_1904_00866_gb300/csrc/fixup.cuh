@@ -60,14 +60,7 @@ __global__ void __launch_bounds__(256, 2) k_refine_stage(const StepParams p,
                                                          int blocks) {
   constexpr int Q = L::Q;
   __shared__ unsigned pre[kMaxRefineBlocks + 1];
-  for (int b = threadIdx.x; b < blocks; b += blockDim.x)
-    pre[b + 1] = p.refine_counts[b];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    pre[0] = 0u;
-    for (int b = 1; b <= blocks; ++b) pre[b] += pre[b - 1];
-  }
-  __syncthreads();
+  block_prefix(p.refine_counts, blocks, pre);
   const unsigned total = pre[blocks];
   const unsigned seg = p.refine_cap / (unsigned)blocks;
   const bool shifted = sizeof(S) == 2 || !p.unshifted;

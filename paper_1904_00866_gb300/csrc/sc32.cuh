@@ -427,6 +427,51 @@ __device__ __forceinline__ void defer_undecided(const StepParams& p,
               node, over ? kNodeRefine : kNodeDone);
 }
 
+// Exclusive prefix sums pre[0..n] of counts[0..n-1] (n <= kMaxRefineBlocks)
+// in shared memory, computed by the whole block (blockDim.x a multiple of
+// 32, at most 1024): each thread sums a run of consecutive counts, the run
+// totals are scanned with warp shuffles and once more across the warps.
+// Every thread of the block must call; ends with a block barrier.
+__device__ __forceinline__ void block_prefix(const unsigned* counts, int n,
+                                             unsigned* pre) {
+  __shared__ unsigned warp_tot[32];
+  const int T = blockDim.x, t = threadIdx.x;
+  const int run = (n + T - 1) / T;   // <= 8 for n <= 2048, T = 256
+  const int b0 = t * run;
+  unsigned sum = 0u;
+  for (int k = 0; k < run; ++k)
+    if (b0 + k < n) sum += counts[b0 + k];
+  // inclusive scan of the run totals within the warp
+  const int lane = t & 31, w = t >> 5;
+  unsigned inc = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
+  }
+  if (lane == 31) warp_tot[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    const int nw = T >> 5;
+    unsigned v = lane < nw ? warp_tot[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
+    }
+    if (lane < nw) warp_tot[lane] = v;   // inclusive over the warps
+  }
+  __syncthreads();
+  unsigned acc = inc - sum + (w > 0 ? warp_tot[w - 1] : 0u);
+  for (int k = 0; k < run; ++k)
+    if (b0 + k < n) {
+      pre[b0 + k] = acc;
+      acc += counts[b0 + k];
+    }
+  if (t == T - 1) pre[n] = warp_tot[(T >> 5) - 1];
+  __syncthreads();
+}
+
 // Block prologue / epilogue of the buffer: the block's entry counter in
 // shared memory starts at zero; at the end the number of entries the block
 // wrote goes to refine_counts[blockIdx.x] (0 when unused).
@@ -441,8 +486,11 @@ __device__ __forceinline__ void refine_block_end(const StepParams& p,
     p.refine_counts[blockIdx.x] = min(*block_count, p.refine_cap / gridDim.x);
 }
 
+// D2Q9 nodes need about half the registers of D3Q27 nodes: more resident
+// blocks keep more gathers in flight (4 per SM, 3 with the statistics)
 template <class L, bool SHIFTED, int DIAG, int CHECK>
-__global__ void __launch_bounds__(kSc32Threads, 2)
+__global__ void __launch_bounds__(kSc32Threads,
+                                  L::Q == 9 ? (DIAG ? 3 : 4) : 2)
     k_sc32(const StepParams p) {
   constexpr int Q = L::Q;
   extern __shared__ float smem[];   // [2][Q][256]
