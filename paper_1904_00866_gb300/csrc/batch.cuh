@@ -359,7 +359,6 @@ __global__ void __launch_bounds__(256) k_batch_refine(const BatchParams bp,
     pp.corr_rho = 0.0f;
     Acc acc;
     acc.init();
-    bool done;
     auto run = [&](auto lat) {
       using L = decltype(lat);
       float v[L::Q + 3];
@@ -372,11 +371,16 @@ __global__ void __launch_bounds__(256) k_batch_refine(const BatchParams bp,
         if (4 * j + 3 < L::Q + 3) v[4 * j + 3] = t.w;
       }
       float (&vq)[L::Q] = *reinterpret_cast<float (*)[L::Q]>(v);
-      return refine_deferred<L, true, DIAG, 0>(
-          pp, vq, node, ap, acc,
-          [&](int i, float val) { out[(size_t)i * m.n + node] = val; });
+      auto out32 = [&](int i, float val) { out[(size_t)i * m.n + node] = val; };
+      // the double-float series pass for nodes the FP32 series leaves open
+      int st = refine_deferred<L, true, DIAG, 0, false>(pp, vq, node, ap, acc,
+                                                        out32);
+      if (st == kStageRetry)
+        st = refine_deferred<L, true, DIAG, 0, true>(pp, vq, node, ap, acc,
+                                                     out32);
+      return st == kStageDone;
     };
-    done = m.lattice == 1 ? run(D3Q27{}) : run(D2Q9{});
+    const bool done = m.lattice == 1 ? run(D3Q27{}) : run(D2Q9{});
     if (!done) {
       const unsigned q = atomicAdd(&bp.far_count[bp.step & 1], 1u);
       if (q < bp.far_cap)
@@ -451,8 +455,13 @@ __global__ void __launch_bounds__(256) k_batch_fixup(const BatchParams bp) {
           auto store32 = [&](int i, float val) {
             out[(size_t)i * m.n + node] = val;
           };
-          return refine_deferred<L, true, DIAG, 0>(
-              pp, v, node, __int_as_float(0x7fc00000), acc, store32);
+          const float nan = __int_as_float(0x7fc00000);
+          int st = refine_deferred<L, true, DIAG, 0, false>(pp, v, node, nan,
+                                                            acc, store32);
+          if (st == kStageRetry)
+            st = refine_deferred<L, true, DIAG, 0, true>(pp, v, node, nan,
+                                                         acc, store32);
+          return st == kStageDone;
         };
         need64 = !(m.lattice == 1 ? run(D3Q27{}) : run(D2Q9{}));
         if (DIAG && !need64) member_stats_add(bp, mi, m, acc, false);

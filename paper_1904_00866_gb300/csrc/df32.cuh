@@ -94,6 +94,28 @@ __device__ __forceinline__ DF<T> df_mul(DF<T> a, T b) {
   return fast_two_sum(p.hi, fma_(a.lo, b, p.lo));
 }
 
+// a / b with b > 0 normal: q1 from the approximate reciprocal (relative
+// error below 2^-22), the residual a - q1 b in double-float (TwoProd exact),
+// then the correction q2 = residual / b.hi; relative error below 2^-44 for
+// |lo| <= u |hi| on both inputs.
+__device__ __forceinline__ float rcp_df_(float y) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y));
+  return r;
+}
+__device__ __forceinline__ float2 rcp_df_(float2 y) {
+  return make_float2(rcp_df_(y.x), rcp_df_(y.y));
+}
+template <class T>
+__device__ __forceinline__ DF<T> df_div(DF<T> a, DF<T> b) {
+  const T rb = rcp_df_(b.hi);
+  const T q1 = mul_(a.hi, rb);
+  const DF<T> p = two_prod(q1, b.hi);
+  // residual a - q1 b = (a.hi - p.hi) - p.lo + a.lo - q1 b.lo
+  const T res = sub_(add_(sub_(sub_(a.hi, p.hi), p.lo), a.lo), mul_(q1, b.lo));
+  return fast_two_sum(q1, mul_(res, rb));
+}
+
 template <class T>
 __device__ __forceinline__ DF<T> df_neg(DF<T> a) {
   return {neg_(a.hi), neg_(a.lo)};

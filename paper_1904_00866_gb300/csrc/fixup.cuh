@@ -13,6 +13,7 @@
 //     resets the other parity's counter for the next step (stream order
 //     makes that counter idle here).
 #pragma once
+#include <type_traits>
 #include "sc32.cuh"
 #include "warp64.cuh"
 
@@ -21,14 +22,15 @@ namespace elbm {
 // Second stage of one deferred node from its stored values v[] (FP32
 // storage: the stored value; FP16: the decoded deviation); the kernel wrote
 // it with the provisional alpha ap (NaN: unknown, recomputed).  Returns
-// false when the node is still undecided (left to the FP64 path).
-template <class L, bool SHIFTED, int DIAG, int CHECK, class Out>
-__device__ __forceinline__ bool refine_deferred(const StepParams& p,
-                                                const float (&v)[L::Q],
-                                                long long node, float ap,
-                                                Acc& acc, Out out) {
+// the second stage's status (kStageDone, kStageRetry: run again with DFS,
+// kStageFP64: left to the FP64 path).
+template <class L, bool SHIFTED, int DIAG, int CHECK, bool DFS, class Out>
+__device__ __forceinline__ int refine_deferred(const StepParams& p,
+                                               const float (&v)[L::Q],
+                                               long long node, float ap,
+                                               Acc& acc, Out out) {
   auto in = [&](int i) { return v[i]; };
-  return second_stage32<L, SHIFTED, DIAG, CHECK>(
+  return second_stage32<L, SHIFTED, DIAG, CHECK, DFS>(
       in, (float)p.rho0, (float)p.beta, p.corr_rho, p.corr,
       p.alpha_map ? p.alpha_map + node : nullptr, ap, out,
       [&](const N32<L>& r) {
@@ -49,12 +51,13 @@ __device__ __forceinline__ bool refine_deferred(const StepParams& p,
 // Second stage of the undecided nodes in the buffer (S: the storage type,
 // float or half_t).  Block b of the stream-collide launch (`blocks`
 // blocks) wrote refine_counts[b] entries from b (refine_cap / blocks) on;
-// every
-// block of this kernel forms their prefix sums in shared memory and takes
-// entries k with a grid stride.  The double-float stage decides (and
-// rewrites the populations its alpha changes); a node it leaves undecided
-// joins the deferred-node queue, so the FP64 fixup that follows collides
-// it with full warps instead of one lane of a warp here.
+// every block of this kernel forms their prefix sums in shared memory and
+// takes entries k with a grid stride.  The double-float stage decides (and
+// rewrites the populations its alpha changes); the few nodes its FP32
+// series leaves open join the deferred-node queue tagged, so that the
+// fixup (whose register budget holds it) runs them again with the leading
+// terms of the series in double-float and collides the rest in FP64 with
+// a whole warp.
 template <class L, class S, int DIAG, int CHECK>
 __global__ void __launch_bounds__(256, 2) k_refine_stage(const StepParams p,
                                                          int blocks) {
@@ -93,24 +96,28 @@ __global__ void __launch_bounds__(256, 2) k_refine_stage(const StepParams p,
     for (int i = 0; i < Q; ++i) v[i] = w[i];
     const long long node = __float_as_uint(w[Q]);
     const float ap = w[Q + 1];
-    bool done;
+    int st;
     if constexpr (sizeof(S) == 2) {
-      done = refine_deferred<L, true, DIAG, CHECK>(
+      st = refine_deferred<L, true, DIAG, CHECK, false>(
           p, v, node, ap, acc, [&](int i, float val) {
             reinterpret_cast<unsigned short*>(p.out_pop[i])[node] =
                 h16_bits<L>(val, i);
           });
     } else {
       auto out = [&](int i, float val) { p.out_pop[i][node] = val; };
-      done = shifted ? refine_deferred<L, true, DIAG, CHECK>(p, v, node, ap,
-                                                             acc, out)
-                     : refine_deferred<L, false, DIAG, CHECK>(p, v, node, ap,
-                                                              acc, out);
+      st = shifted
+               ? refine_deferred<L, true, DIAG, CHECK, false>(p, v, node, ap,
+                                                              acc, out)
+               : refine_deferred<L, false, DIAG, CHECK, false>(p, v, node, ap,
+                                                               acc, out);
     }
-    if (!done) {
+    if (st != kStageDone) {
+      // kStageRetry: tagged, so that the fixup runs the double-float
+      // series pass (in its larger register budget) before any FP64
       const unsigned q = atomicAdd(&p.far_count[p.parity], 1u);
       if (q < p.far_cap)
-        p.far_queue[q] = (unsigned)node;
+        p.far_queue[q] =
+            (unsigned)node | (st == kStageRetry ? kTagRefine : 0u);
       else
         atomicOr(p.err_flags, NF_BAD_NONFINITE);   // cannot happen: cap = n
     }
@@ -177,10 +184,16 @@ __global__ void __launch_bounds__(256) k_far_fixup(const StepParams p) {
         }
         const float ap = __int_as_float(0x7fc00000);   // NaN: recomputed
         auto out = [&](int i, float val) { out_s(node, i, val); };
-        need64 = !(shifted ? refine_deferred<L, true, DIAG, CHECK>(
-                                 p, v, node, ap, acc, out)
-                           : refine_deferred<L, false, DIAG, CHECK>(
-                                 p, v, node, ap, acc, out));
+        auto run = [&](auto dfs) {
+          constexpr bool DFS = decltype(dfs)::value;
+          return shifted ? refine_deferred<L, true, DIAG, CHECK, DFS>(
+                               p, v, node, ap, acc, out)
+                         : refine_deferred<L, false, DIAG, CHECK, DFS>(
+                               p, v, node, ap, acc, out);
+        };
+        int st = run(std::false_type{});
+        if (st == kStageRetry) st = run(std::true_type{});
+        need64 = st != kStageDone;
       }
     }
     // FP64 nodes of this round: with many of them in the warp (the first

@@ -108,14 +108,21 @@ constexpr float kUMax32 = 0.25f;
 // from an evaluation's bounds (2^-16); a wider one goes to the next stage.
 constexpr float kChordWidth = 1.52587890625e-05f;
 
-// 1 / y by the SFU (rcp.approx.ftz.f32, relative error below 2^-23).
-// The other approximate operations below are used with their documented
-// accuracy: rsqrtf within 2 ulp (relative 2^-22), __fdividef within 2 ulp
-// for divisors of normal magnitude.  None of them needs the IEEE
-// division's or square root's special-case path.
+// 1 / y and 1 / sqrt(y) by the SFU (rcp.approx.ftz.f32, relative error
+// below 2^-23; rsqrt.approx.ftz.f32, relative error below 2^-22; subnormal
+// arguments flush to zero, so callers pass normal values).  __fdividef is
+// used within its documented 2 ulp for divisors of normal magnitude.  None
+// of them needs the IEEE division's or square root's special-case path,
+// nor the subnormal scaling of the non-flushing forms (conversion-class
+// instructions, which GB300 issues on its FP64 pipe).
 __device__ __forceinline__ float rcp_approx(float y) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y));
+  return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float y) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y));
   return r;
 }
 __device__ __forceinline__ float2 rcp_approx2(float2 y) {
@@ -214,9 +221,10 @@ __device__ __forceinline__ DH32 series_dh32(const float (&M)[9], bool k8,
          4.0f * uu * (fabsf(M[3]) * (1.0f / 3.0f) + fabsf(M[4]) * (2.0f / 3.0f) +
                       rnd) +
          2.0f * rho * (xabs + Ex) * Ex * Ex;
-  // S1b >= sqrt(rho M2) >= sum f |x|  (Cauchy-Schwarz)
+  // S1b >= sqrt(rho M2) >= sum f |x|  (Cauchy-Schwarz); 1e-15 bounds the
+  // root of any rm <= 1e-30 (no subnormal reaches the reciprocal root)
   const float rm = rho * M2;
-  const float S1b = rm > 0.0f ? rm * rsqrtf(rm) * kUp : 0.0f;
+  const float S1b = rm > 1e-30f ? rm * rsqrt_approx(rm) * kUp : 1e-15f;
   h.e1 = __fdividef(1.01f * Ex * S1b, 1.0f - xabs) * kUp +
          M2 * (gq * (0.5f + xabs) + tr1) + 4.0f * uu * (0.5f * M2 + fabsf(M[3])) +
          2.0f * rho * Ex * Ex;
@@ -313,17 +321,24 @@ __device__ __forceinline__ void exact_moments(float d0,
 // recomputed in double-float arithmetic from the exact moments, so x_i is
 // known to 6.1 u |x_i| + G (1 + Dd)^3 2^-37 instead of the FP32 path's
 // equilibrium rounding, and the decision is retaken with the bounds of that
-// accuracy (series always to k = 8).  A node still undecided (its Delta H(2)
-// within the double-float error of zero) is deferred to the FP64 fixup
-// (NF_FAR).  Writes r.n0 / r.n2 (the more accurate n, used by the
-// relaxation), r.alpha, r.flags (NF_BAND set: the second stage decided)
-// and the moments r.drho, r.rho, r.j.
-template <class L, bool SHIFTED>
+// accuracy (series always to k = 8).  A node this leaves undecided is
+// flagged NF_FAR | NF_REFINE; the DFS variant then evaluates the leading
+// terms of Delta H(2) in double-float too (its resolution is set by the
+// double-float n, ~1e-12 of W_i rho, instead of the FP32 series' ~75 u),
+// and a node still undecided (NF_FAR) goes to the FP64 fixup.  Writes
+// r.n0 / r.n2 (the more accurate n, used by the relaxation), r.alpha,
+// r.flags (NF_BAND set: the second stage decided) and the moments r.drho,
+// r.rho, r.j.
+template <class L, bool SHIFTED, bool DFS = false>
 __device__ __forceinline__ void node32_refine(
     float d0, const float2 (&dd)[npairs<L>()], float rho0, float corr_rho,
     const float* __restrict__ corr, float a_extra, N32<L>& r) {
   constexpr int P = npairs<L>();
   constexpr float uu = 5.9604645e-8f;  // 2^-24
+  // DFS: the leading terms -M3/3 + 2 M4/3 of Delta H(2) in double-float as
+  // well (x_i = n_i / f_i as a double-float quotient), for the nodes the
+  // FP32 series on the double-float n leaves undecided
+  DF<float> m3d = {0.0f, 0.0f}, m4d = {0.0f, 0.0f};
   // exact_moments needs sum |delta_i| < 4
   {
     float2 sa = make_float2(fabsf(dd[0].x), fabsf(dd[0].y));
@@ -366,7 +381,7 @@ __device__ __forceinline__ void node32_refine(
     // s = sqrt(1 + 3u^2) - 1: one Newton step on s^2 + 2s - 3u^2 = 0 from
     // the FP32 value (relative error 9.5 u, squared by the step)
     const float y = fmaf(3.0f * u.hi, u.hi, 1.0f);
-    const float s0 = 3.0f * u.hi * u.hi * rcp_approx(1.0f + y * rsqrtf(y));
+    const float s0 = 3.0f * u.hi * u.hi * rcp_approx(1.0f + y * rsqrt_approx(y));
     const DF<float> sq = two_prod(s0, s0);
     const DF<float> t = two_sum(sq.hi, add_(s0, s0));
     const DF<float> u3 = df_mul(u, 3.0f);
@@ -417,6 +432,13 @@ __device__ __forceinline__ void node32_refine(
       M[k] = pw;
       pw *= x;
     }
+    if (DFS) {
+      const DF<float> fd = df_add(df_mul(wdf(0), rho0), d0);   // f_0
+      const DF<float> xd = df_div(t, fd);
+      const DF<float> n2 = df_mul(df_mul(t, xd), xd);          // f x^3
+      m3d = n2;
+      m4d = df_mul(n2, xd);                                    // f x^4
+    }
   }
   auto pair = [&](int a, int c) { return df_pair(psi[a][c + 1], psi[a][1 - c]); };
   DF<float2> pxy[3][3];
@@ -447,6 +469,19 @@ __device__ __forceinline__ void node32_refine(
     for (int e = 2; e <= 8; ++e) {
       mk[e] = add2(mk[e], pw);
       pw = mul2(pw, x);
+    }
+    if (DFS) {
+      const DF<float2> fd =
+          df_add(df_mul(df_bcast(wdf(i)), f2(rho0)), dd[k]);   // f_i
+      const DF<float2> xd = df_div(t, fd);
+      const DF<float2> n2 = df_mul(df_mul(t, xd), xd);
+      const DF<float2> n3 = df_mul(n2, xd);
+      const DF<float> a3 = df_add(DF<float>{n2.hi.x, n2.lo.x},
+                                  DF<float>{n2.hi.y, n2.lo.y});
+      const DF<float> a4 = df_add(DF<float>{n3.hi.x, n3.lo.x},
+                                  DF<float>{n3.hi.y, n3.lo.y});
+      m3d = df_add(m3d, a3);
+      m4d = df_add(m4d, a4);
     }
   }
 #pragma unroll
@@ -485,11 +520,40 @@ __device__ __forceinline__ void node32_refine(
   const float En = 2.0f * e2u *
                    (G * (opdD * fmaf(3.0f, cpsi, 52.0f) + 33.0f * r0r) + 8.0f);
   const float Ex = 1.01f * (6.1f * uu * xabs + En + G * a_extra);
-  const DH32 h = series_dh32<L::Q>(M, true, xabs, Ex, rho.hi);
+  DH32 h = series_dh32<L::Q>(M, true, xabs, Ex, rho.hi);
+  if (DFS) {
+    // Delta H(2) = [-M3 / 3 + 2 M4 / 3] (double-float) + sum_{k=5..8} c_k M_k
+    // (FP32) + tail.  Errors: x_i within Exd = En + G a_extra + 2^-42 |x_i|
+    // (the double-float n, f_i and quotient), propagated through the
+    // leading terms as M2 (1 + 3 xabs) Exd; their double-float rounding
+    // (2,000 u^2 xabs M2 covers 27 terms of a few operations each); the
+    // FP32 terms k = 5..8 from x within Ex (100 u xabs^3 M2 with their
+    // rounding); the tail beyond k = 8; the final FP32 sum.
+    constexpr float c3h = df_hi(-1.0 / 3.0), c3l = df_lo(-1.0 / 3.0);
+    constexpr float c4h = df_hi(2.0 / 3.0), c4l = df_lo(2.0 / 3.0);
+    const DF<float> lead = df_add(df_mul(m3d, DF<float>{c3h, c3l}),
+                                  df_mul(m4d, DF<float>{c4h, c4l}));
+    const float tail =
+        fmaf(-1.1f, M[5],
+             fmaf(26.0f / 15.0f, M[6], fmaf(-19.0f / 7.0f, M[7],
+                                           (30.0f / 7.0f) * M[8])));
+    const float D2 = lead.hi + (lead.lo + tail);
+    const float Exd = 1.01f * (En + G * a_extra + 2.3e-13f * xabs);
+    const float r2 = 2.0f * xabs;
+    const float r2_7 = r2 * r2 * r2 * r2 * r2 * r2 * r2;
+    const float tr2 = __fdividef(r2_7, 18.0f * (1.0f - r2)) * kUp;
+    const float x3 = xabs * xabs * xabs;
+    h.D2 = D2;
+    h.e2 = 1.1f * (M[2] * ((1.0f + 3.0f * xabs) * Exd + 2.0e3f * e2u * xabs +
+                           100.0f * uu * x3 + tr2) +
+                   2.0f * uu * (fabsf(lead.hi) + fabsf(tail)) +
+                   2.0f * rho.hi * (xabs + Exd) * Exd * Exd);
+  }
   float alpha = 1.0f;
   const int k = decide32(h, alpha, kChordWidth);
   if (k == kUndecided) {
-    r.flags = NF_FAR;
+    // the double-float leading terms (DFS) may still decide it
+    r.flags = DFS ? NF_FAR : (NF_FAR | NF_REFINE);
     return;
   }
   r.alpha = alpha;
@@ -546,10 +610,10 @@ __device__ __forceinline__ void node32_formula(
     const float u = j[a] * inv_rho;
     U = fmaxf(U, fabsf(u));
     // s = 3u^2 / (1 + sqrt(1 + 3u^2)), relative error <= 9.5 u (numerator
-    // 2 u, 1 + 3u^2 2 u, its root via rsqrtf 6 u, 1 + root 4.5 u, the
+    // 2 u, 1 + 3u^2 2 u, its root via rsqrt_approx 6 u, 1 + root 4.5 u, the
     // reciprocal 2 u, the product u)
     const float y = fmaf(3.0f * u, u, 1.0f);
-    const float s = 3.0f * u * u * rcp_approx(1.0f + y * rsqrtf(y));
+    const float s = 3.0f * u * u * rcp_approx(1.0f + y * rsqrt_approx(y));
     dp[a] = fmaf(3.0f, u, 2.0f * s);
     dm[a] = fmaf(-3.0f, u, 2.0f * s);
     dz[a] = -s;

@@ -643,7 +643,10 @@ elbm_status elbm_step(elbm_handle* h, long long nsteps, elbm_alpha_mode mode) {
     int rows = grid;
     if (fp32_formula) {
       StepParams pf = p;
-      const int fgrid = grid;
+      // the second stage and the fixup run at most 2 blocks per SM
+      // (their register budgets), so a larger grid only adds waves of
+      // blocks with nothing to do
+      const int fgrid = std::min(grid, max_grid_rows() / 4);
       if (p.exact && p.refine_cap) {
         // second stage of the undecided nodes the step buffered
         pf.partials = h->partials + (size_t)rows * NSTAT;

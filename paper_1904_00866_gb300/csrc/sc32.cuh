@@ -305,15 +305,18 @@ __device__ __forceinline__ unsigned sc32_node_in(
 // map and the statistics.  Both relaxations use the double-float n, so a
 // population the decided alpha does not change at storage precision keeps
 // the provisional value, which differs from it by at most the rounding of
-// the FP32 n.  Returns false when the node is still undecided (left to the
-// FP64 path, which rewrites all of it).
-template <class L, bool SHIFTED, int DIAG, int CHECK, class In, class Out,
-          class Stat>
-__device__ __forceinline__ bool second_stage32(In in, float rho0f,
-                                               float beta, float corr_rho,
-                                               const float* __restrict__ corr,
-                                               float* amap, float ap, Out out,
-                                               Stat stat) {
+// the FP32 n.  Returns kStageDone, kStageRetry (still undecided by the FP32
+// series on the double-float n: the DFS pass, which also evaluates the
+// leading terms in double-float, may decide it) or kStageFP64 (left to the
+// FP64 path, which rewrites all of it).  Nothing is written unless done.
+enum { kStageDone = 0, kStageRetry = 1, kStageFP64 = 2 };
+template <class L, bool SHIFTED, int DIAG, int CHECK, bool DFS, class In,
+          class Out, class Stat>
+__device__ __forceinline__ int second_stage32(In in, float rho0f, float beta,
+                                              float corr_rho,
+                                              const float* __restrict__ corr,
+                                              float* amap, float ap, Out out,
+                                              Stat stat) {
   constexpr int P = npairs<L>();
   float d0, a_extra;
   float2 dd[P];
@@ -327,13 +330,14 @@ __device__ __forceinline__ bool second_stage32(In in, float rho0f,
   N32<L> t;
   t.flags = 0u;
   t.alpha = 1.0f;
-  node32_refine<L, SHIFTED>(d0, dd, rho0f, corr_rho, corr, a_extra, t);
-  if (t.flags & NF_FAR) return false;
+  node32_refine<L, SHIFTED, DFS>(d0, dd, rho0f, corr_rho, corr, a_extra, t);
+  if (t.flags & NF_FAR)
+    return (t.flags & NF_REFINE) ? kStageRetry : kStageFP64;
   if (t.alpha != ap)
     relax_update32<L, SHIFTED>(t, ap, t.alpha, d0, dd, rho0f, beta, out);
   if (amap) *amap = t.alpha;
   stat(t);
-  return true;
+  return kStageDone;
 }
 
 // Buffer of undecided nodes for the second stage: one record of
