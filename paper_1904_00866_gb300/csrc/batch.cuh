@@ -354,6 +354,8 @@ __global__ void __launch_bounds__(256) k_batch_refine(const BatchParams bp,
     StepParams pp;
     pp.beta = m.beta64;
     pp.rho0 = m.rho0;
+    pp.betaf = m.beta;
+    pp.rho0f = m.rho0f;
     pp.alpha_map = m.alpha_map;
     pp.unshifted = 0;
     pp.corr_rho = 0.0f;
@@ -416,6 +418,8 @@ __global__ void __launch_bounds__(256) k_batch_fixup(const BatchParams bp) {
     StepParams pp;
     pp.beta = m.beta64;
     pp.rho0 = m.rho0;
+    pp.betaf = m.beta;
+    pp.rho0f = m.rho0f;
     pp.err_flags = bp.err_flags;
     pp.secant_iters = 1;
     pp.alpha_map = m.alpha_map;

@@ -31,7 +31,7 @@ __device__ __forceinline__ int refine_deferred(const StepParams& p,
                                                Acc& acc, Out out) {
   auto in = [&](int i) { return v[i]; };
   return second_stage32<L, SHIFTED, DIAG, CHECK, DFS>(
-      in, (float)p.rho0, (float)p.beta, p.corr_rho, p.corr,
+      in, p.rho0f, p.betaf, p.corr_rho, p.corr,
       p.alpha_map ? p.alpha_map + node : nullptr, ap, out,
       [&](const N32<L>& r) {
         if (!DIAG) return;

@@ -553,6 +553,8 @@ elbm_status elbm_step(elbm_handle* h, long long nsteps, elbm_alpha_mode mode) {
   p.tiles = (long long)p.chunks * h->ny * h->nz;
   p.beta = h->beta;
   p.rho0 = h->dtype == ELBM_FP64 ? 0.0 : h->rho0;
+  p.betaf = (float)p.beta;
+  p.rho0f = (float)p.rho0;
   p.unshifted = h->dtype == ELBM_FP32;
   if (p.unshifted) {
     const float r0 = (float)h->rho0;

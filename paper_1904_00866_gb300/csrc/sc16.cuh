@@ -49,8 +49,8 @@ __global__ void __launch_bounds__(kSc32Threads, 2)
   constexpr int Q = L::Q;
   extern __shared__ unsigned smem_w[];   // [2][Q][256] words
   const unsigned ntiles = (unsigned)((p.n + kSc32Threads - 1) / kSc32Threads);
-  const float rho0f = (float)p.rho0;
-  const float beta = (float)p.beta;
+  const float rho0f = p.rho0f;
+  const float beta = p.betaf;
   Acc32 acc;
   if (DIAG) acc.init();
   __shared__ unsigned s_refine;     // this block's undecided-node entries

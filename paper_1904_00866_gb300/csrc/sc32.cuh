@@ -500,8 +500,8 @@ __global__ void __launch_bounds__(kSc32Threads,
   extern __shared__ float smem[];   // [2][Q][256]
   __shared__ unsigned s_refine;     // this block's undecided-node entries
   const unsigned ntiles = (unsigned)((p.n + kSc32Threads - 1) / kSc32Threads);
-  const float rho0f = (float)p.rho0;
-  const float beta = (float)p.beta;
+  const float rho0f = p.rho0f;
+  const float beta = p.betaf;
   Acc32 acc;
   if (DIAG) acc.init();
   refine_block_begin(&s_refine);

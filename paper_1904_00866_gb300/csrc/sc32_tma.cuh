@@ -127,8 +127,8 @@ __global__ void __launch_bounds__(256, 2) k_sc32_tma(const StepParams p) {
   __shared__ unsigned released[S];
   const unsigned chunks = (unsigned)p.nx / 256u;
   const unsigned ntiles = chunks * (unsigned)p.ny * (unsigned)p.nz;
-  const float rho0f = (float)p.rho0;
-  const float beta = (float)p.beta;
+  const float rho0f = p.rho0f;
+  const float beta = p.betaf;
   const int lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int st = 0; st < S; ++st) {

@@ -100,8 +100,8 @@ __global__ void __launch_bounds__(kWideThreads, 3)
   float* my = smem_wide + w * 2 * S;
   const unsigned nseg = (unsigned)(p.n / kWideSeg);
   const unsigned nwarps = gridDim.x * kWideWarps;
-  const float rho0f = (float)p.rho0;
-  const float beta = (float)p.beta;
+  const float rho0f = p.rho0f;
+  const float beta = p.betaf;
   Acc32 acc;
   if (DIAG) acc.init();
   __shared__ unsigned s_refine;     // this block's undecided-node entries

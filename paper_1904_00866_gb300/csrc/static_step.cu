@@ -140,6 +140,8 @@ extern "C" elbm_status elbm_step_static(
   const double cs2 = 1.0 / 3.0;
   p.beta = cs2 / (2.0 * nu + cs2);
   p.rho0 = (double)(float)rho0;
+  p.betaf = (float)p.beta;
+  p.rho0f = (float)p.rho0;
   p.unshifted = 0;
   p.secant_iters = 1;
   // the exact decision of elbm_step's default; without a buffer the

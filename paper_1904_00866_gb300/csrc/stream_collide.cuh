@@ -73,6 +73,10 @@ struct StepParams {
   long long tiles;        // chunks * ny * nz
   double beta;
   double rho0;            // shift reference (0 for FP64 storage)
+  // the same rounded to FP32 on the host: a kernel that converted them
+  // itself could repeat the conversion (an FP64-pipe instruction) per node
+  // to save the registers
+  float betaf, rho0f;
   int unshifted;          // FP32 storage of f itself (not f - W rho0)
   float corr_rho;         // unshifted: sum_i fl(W_i rho0) - rho0
   float corr[27];         // unshifted: W_i rho0 - fl(W_i rho0)
