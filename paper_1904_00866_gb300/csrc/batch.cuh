@@ -408,6 +408,7 @@ __global__ void __launch_bounds__(256) k_batch_fixup(const BatchParams bp) {
   const unsigned W = gridDim.x * (blockDim.x >> 5);
   const unsigned wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const LanePop lp27 = lane_pop<D3Q27>(lane), lp9 = lane_pop<D2Q9>(lane);
+  const bool bulk = count > gridDim.x * blockDim.x;
   auto coords = [](const MemberDesc& m, unsigned node, int& x, int& y,
                    int& z) {
     x = (int)(node % (unsigned)m.nx);
@@ -462,7 +463,8 @@ __global__ void __launch_bounds__(256) k_batch_fixup(const BatchParams bp) {
           const float nan = __int_as_float(0x7fc00000);
           int st = refine_deferred<L, true, DIAG, 0, false>(pp, v, node, nan,
                                                             acc, store32);
-          if (st == kStageRetry)
+          // as in k_far_fixup: no series pass on a queue longer than the grid
+          if (st == kStageRetry && !bulk)
             st = refine_deferred<L, true, DIAG, 0, true>(pp, v, node, nan,
                                                          acc, store32);
           return st == kStageDone;

@@ -146,6 +146,7 @@ __global__ void __launch_bounds__(256) k_far_fixup(const StepParams p) {
   const unsigned W = gridDim.x * (blockDim.x >> 5);
   const unsigned wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const LanePop lp = lane_pop<L>(lane);
+  const bool bulk = count > gridDim.x * blockDim.x;
   Acc acc;
   acc.init();
   auto coords = [&](long long node, int& x, int& y, int& z) {
@@ -192,7 +193,11 @@ __global__ void __launch_bounds__(256) k_far_fixup(const StepParams p) {
                                p, v, node, ap, acc, out);
         };
         int st = run(std::false_type{});
-        if (st == kStageRetry) st = run(std::true_type{});
+        // the series pass pays off on the few nodes of a developed flow; on
+        // a queue longer than the grid (the first step after
+        // initialisation, where n is rounding noise and the pass decides
+        // few nodes) they go to the FP64 path directly
+        if (st == kStageRetry && !bulk) st = run(std::true_type{});
         need64 = st != kStageDone;
       }
     }
