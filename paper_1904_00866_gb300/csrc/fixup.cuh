@@ -161,6 +161,87 @@ __global__ void __launch_bounds__(256) k_far_fixup(const StepParams p) {
     else
       p.out_pop[i][node] = val;
   };
+  // FP64 FORMULA of one node in this thread
+  auto fp64_lane = [&](long long node) {
+    int x, y, z;
+    coords(node, x, y, z);
+    Node64<L> nd;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const long long src = src_index<L>(p, i, x, y, z);
+      double vi;
+      if constexpr (sizeof(S) == 2)
+        vi = h16_dev<L>(reinterpret_cast<const unsigned short*>(
+                            p.in_pop[i])[src],
+                        i);
+      else
+        vi = p.in_pop[i][src];
+      nd.f[i] = shifted ? L::w(i) * p.rho0 + vi : vi;
+    }
+    auto store_s = [&](int i, double val) {
+      if (i < 0) {
+        p.alpha_map[node] = (float)val;
+      } else if constexpr (sizeof(S) == 2) {
+        reinterpret_cast<half_t*>(p.out_pop[i])[node] =
+            h16_from_dev<L>(val - L::w(i) * p.rho0, i);
+      } else {
+        p.out_pop[i][node] =
+            (float)(p.unshifted ? val : val - L::w(i) * p.rho0);
+      }
+    };
+    if (DIAG) acc.far += 1;
+    collide64<L, MODE_FORMULA, CHECK>(nd, p, true, acc, DIAG != 0, store_s);
+  };
+  // FP64 FORMULA of node nd by the whole warp (every lane calls)
+  auto fp64_warp = [&](long long nd) {
+    int x, y, z;
+    coords(nd, x, y, z);
+    double f = 0.0;
+    if (lp.on) {
+      int xs = x - lp.c[0], ys = y - lp.c[1], zs = z - lp.c[2];
+      xs = xs < 0 ? xs + p.nx : (xs >= p.nx ? xs - p.nx : xs);
+      ys = ys < 0 ? ys + p.ny : (ys >= p.ny ? ys - p.ny : ys);
+      zs = zs < 0 ? zs + p.nz : (zs >= p.nz ? zs - p.nz : zs);
+      const long long src = ((long long)zs * p.ny + ys) * p.nx + xs;
+      if constexpr (sizeof(S) == 2) {
+        const unsigned short b =
+            reinterpret_cast<const unsigned short*>(p.in_pop[lane])[src];
+        f = (double)(__half2float(__ushort_as_half(b)) * lp.hscale_inv);
+      } else {
+        f = (double)p.in_pop[lane][src];
+      }
+      if (shifted) f += lp.w * p.rho0;
+    }
+    const Warp64 r = formula64_warp<L>(lp, f, p.beta, [&](double val) {
+      if constexpr (sizeof(S) == 2)
+        reinterpret_cast<half_t*>(p.out_pop[lane])[nd] =
+            __double2half((val - lp.w * p.rho0) * (double)lp.hscale);
+      else
+        p.out_pop[lane][nd] = (float)(p.unshifted ? val : val - lp.w * p.rho0);
+    });
+    if (lane == 0) {
+      if (DIAG) acc.far += 1;
+      if (r.flags & (NF_BAD_NEG | NF_BAD_NONFINITE)) {
+        atomicOr(p.err_flags, r.flags);
+      } else {
+        if (p.alpha_map) p.alpha_map[nd] = (float)r.alpha;
+        if (DIAG) {
+          acc.add_moments(r.rho - p.rho0, r.j, r.rho);
+          acc.add_alpha(r.alpha, r.flags, 0);
+        }
+      }
+    }
+  };
+  // bulk queues: this warp's pending FP64 nodes (warp-uniform count)
+  __shared__ unsigned pend_s[8][32];   // 256 threads: 8 warps
+  unsigned* pend = pend_s[threadIdx.x >> 5];
+  int npend = 0;
+  auto flush = [&]() {   // every lane calls
+    __syncwarp();
+    if (lane < npend) fp64_lane((long long)pend[lane]);
+    __syncwarp();
+    npend = 0;
+  };
   for (unsigned base = 0; base < count; base += 32u * W) {
     const unsigned k = base + (unsigned)lane * W + wid;
     bool need64 = false;
@@ -201,86 +282,38 @@ __global__ void __launch_bounds__(256) k_far_fixup(const StepParams p) {
         need64 = st != kStageDone;
       }
     }
-    // FP64 nodes of this round: with many of them in the warp (the first
-    // step after initialisation) one per lane costs less FP64 issue than
-    // one per warp; with few (developed flows) one per warp ends sooner.
-    // The check's statistics need each node in one thread.
+    // FP64 nodes of this round.  Per lane a node costs ~75 FP64 warp
+    // instructions of its warp (2,400 shared by 32 lanes), per warp ~460:
+    // one per warp ends sooner when a warp has few such nodes (developed
+    // flows), one per lane costs less FP64 issue in bulk.  On a queue
+    // longer than the grid (the first step after initialisation, ~1 % of
+    // the nodes in FP64) each warp collects its FP64 nodes in shared memory
+    // and runs them 32 at a time, one per lane.  The check's statistics
+    // need each node in one thread.
     const unsigned m64 = __ballot_sync(0xffffffffu, need64);
-    if (CHECK != 0 || __popc(m64) > 16) {
-      if (!need64) continue;
-      int x, y, z;
-      coords(node, x, y, z);
-      Node64<L> nd;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const long long src = src_index<L>(p, i, x, y, z);
-        double vi;
-        if constexpr (sizeof(S) == 2)
-          vi = h16_dev<L>(reinterpret_cast<const unsigned short*>(
-                              p.in_pop[i])[src],
-                          i);
-        else
-          vi = p.in_pop[i][src];
-        nd.f[i] = shifted ? L::w(i) * p.rho0 + vi : vi;
-      }
-      auto store_s = [&](int i, double val) {
-        if (i < 0) {
-          p.alpha_map[node] = (float)val;
-        } else if constexpr (sizeof(S) == 2) {
-          reinterpret_cast<half_t*>(p.out_pop[i])[node] =
-              h16_from_dev<L>(val - L::w(i) * p.rho0, i);
-        } else {
-          p.out_pop[i][node] =
-              (float)(p.unshifted ? val : val - L::w(i) * p.rho0);
-        }
-      };
-      if (DIAG) acc.far += 1;
-      collide64<L, MODE_FORMULA, CHECK>(nd, p, true, acc, DIAG != 0, store_s);
+    if (CHECK != 0 || (!bulk && __popc(m64) > 16)) {
+      if (need64) fp64_lane(node);
+    } else if (bulk) {
+      const int nk = __popc(m64);
+      if (npend + nk > 32) flush();
+      if (need64) pend[npend + __popc(m64 & ((1u << lane) - 1u))] =
+          (unsigned)node;
+      npend += nk;
     } else {
       unsigned m = m64;
       while (m) {
         const int src_lane = __ffs(m) - 1;
         m &= m - 1;
-        const long long nd = __shfl_sync(0xffffffffu, node, src_lane);
-        int x, y, z;
-        coords(nd, x, y, z);
-        double f = 0.0;
-        if (lp.on) {
-          int xs = x - lp.c[0], ys = y - lp.c[1], zs = z - lp.c[2];
-          xs = xs < 0 ? xs + p.nx : (xs >= p.nx ? xs - p.nx : xs);
-          ys = ys < 0 ? ys + p.ny : (ys >= p.ny ? ys - p.ny : ys);
-          zs = zs < 0 ? zs + p.nz : (zs >= p.nz ? zs - p.nz : zs);
-          const long long src = ((long long)zs * p.ny + ys) * p.nx + xs;
-          if constexpr (sizeof(S) == 2) {
-            const unsigned short b =
-                reinterpret_cast<const unsigned short*>(p.in_pop[lane])[src];
-            f = (double)(__half2float(__ushort_as_half(b)) * lp.hscale_inv);
-          } else {
-            f = (double)p.in_pop[lane][src];
-          }
-          if (shifted) f += lp.w * p.rho0;
-        }
-        const Warp64 r = formula64_warp<L>(lp, f, p.beta, [&](double val) {
-          if constexpr (sizeof(S) == 2)
-            reinterpret_cast<half_t*>(p.out_pop[lane])[nd] =
-                __double2half((val - lp.w * p.rho0) * (double)lp.hscale);
-          else
-            p.out_pop[lane][nd] =
-                (float)(p.unshifted ? val : val - lp.w * p.rho0);
-        });
-        if (lane == 0) {
-          if (DIAG) acc.far += 1;
-          if (r.flags & (NF_BAD_NEG | NF_BAD_NONFINITE)) {
-            atomicOr(p.err_flags, r.flags);
-          } else {
-            if (p.alpha_map) p.alpha_map[nd] = (float)r.alpha;
-            if (DIAG) {
-              acc.add_moments(r.rho - p.rho0, r.j, r.rho);
-              acc.add_alpha(r.alpha, r.flags, 0);
-            }
-          }
-        }
+        fp64_warp(__shfl_sync(0xffffffffu, node, src_lane));
       }
+    }
+  }
+  if (npend > 0) {   // bulk remainder: few nodes run one per warp
+    __syncwarp();
+    if (npend > 5) {
+      flush();
+    } else {
+      for (int j = 0; j < npend; ++j) fp64_warp((long long)pend[j]);
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) p.far_count[p.parity ^ 1] = 0u;
