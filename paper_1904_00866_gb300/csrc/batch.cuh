@@ -428,6 +428,94 @@ __global__ void __launch_bounds__(256) k_batch_fixup(const BatchParams bp) {
     pp.corr_rho = 0.0f;
     return pp;
   };
+  // FP64 FORMULA of queue entry ee in this thread
+  auto fp64_lane = [&](unsigned long long ee) {
+    const int mi = (int)(ee >> 32);
+    const unsigned node = (unsigned)(ee & 0xffffffffu) & ~kTagRefine;
+    const MemberDesc& m = bp.members[mi];
+    const float* in = pick(m, m.parity0 + bp.step);
+    float* out = pick(m, m.parity0 + bp.step + 1);
+    StepParams g;   // geometry for src_index
+    g.nx = m.nx;
+    g.ny = m.ny;
+    g.nz = m.nz;
+    int x, y, z;
+    coords(m, node, x, y, z);
+    Acc acc;
+    acc.init();
+    const StepParams pp = params(m);
+    auto run = [&](auto lat) {
+      using L = decltype(lat);
+      Node64<L> nd;
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i)
+        nd.f[i] = L::w(i) * m.rho0 +
+                  (double)in[(size_t)i * m.n + src_index<L>(g, i, x, y, z)];
+      auto store = [&](int i, double val) {
+        if (i < 0)
+          m.alpha_map[node] = (float)val;
+        else
+          out[(size_t)i * m.n + node] = (float)(val - L::w(i) * m.rho0);
+      };
+      collide64<L, MODE_FORMULA, 0>(nd, pp, true, acc, DIAG != 0, store);
+    };
+    if (m.lattice == 1)
+      run(D3Q27{});
+    else
+      run(D2Q9{});
+    if (DIAG) member_stats_add(bp, mi, m, acc, true);
+  };
+  // FP64 FORMULA of queue entry ee by the whole warp (every lane calls)
+  auto fp64_warp = [&](unsigned long long ee) {
+    const int mi = (int)(ee >> 32);
+    const unsigned node = (unsigned)(ee & 0xffffffffu) & ~kTagRefine;
+    const MemberDesc& m = bp.members[mi];
+    const float* in = pick(m, m.parity0 + bp.step);
+    float* out = pick(m, m.parity0 + bp.step + 1);
+    int x, y, z;
+    coords(m, node, x, y, z);
+    auto run = [&](auto lat, const LanePop& lp) {
+      using L = decltype(lat);
+      double f = 0.0;
+      if (lp.on) {
+        int xs = x - lp.c[0], ys = y - lp.c[1], zs = z - lp.c[2];
+        xs = xs < 0 ? xs + m.nx : (xs >= m.nx ? xs - m.nx : xs);
+        ys = ys < 0 ? ys + m.ny : (ys >= m.ny ? ys - m.ny : ys);
+        zs = zs < 0 ? zs + m.nz : (zs >= m.nz ? zs - m.nz : zs);
+        const size_t src =
+            ((size_t)zs * (size_t)m.ny + (size_t)ys) * (size_t)m.nx +
+            (size_t)xs;
+        f = lp.w * m.rho0 + (double)in[(size_t)lane * m.n + src];
+      }
+      return formula64_warp<L>(lp, f, m.beta64, [&](double val) {
+        out[(size_t)lane * m.n + node] = (float)(val - lp.w * m.rho0);
+      });
+    };
+    const Warp64 r = m.lattice == 1 ? run(D3Q27{}, lp27) : run(D2Q9{}, lp9);
+    if (lane == 0) {
+      if (r.flags & (NF_BAD_NEG | NF_BAD_NONFINITE)) {
+        atomicOr(bp.err_flags, r.flags);
+      } else {
+        if (m.alpha_map) m.alpha_map[node] = (float)r.alpha;
+        if (DIAG) {
+          Acc acc;
+          acc.init();
+          acc.add_moments(r.rho - m.rho0, r.j, r.rho);
+          acc.add_alpha(r.alpha, r.flags, 0);
+          member_stats_add(bp, mi, m, acc, true);
+        }
+      }
+    }
+  };
+  __shared__ unsigned long long pend_s[8][32];   // 256 threads: 8 warps
+  unsigned long long* pend = pend_s[threadIdx.x >> 5];
+  int npend = 0;
+  auto flush = [&]() {   // every lane calls
+    __syncwarp();
+    if (lane < npend) fp64_lane(pend[lane]);
+    __syncwarp();
+    npend = 0;
+  };
   for (unsigned base = 0; base < count; base += 32u * W) {
     const unsigned k = base + (unsigned)lane * W + wid;
     bool need64 = false;
@@ -473,91 +561,32 @@ __global__ void __launch_bounds__(256) k_batch_fixup(const BatchParams bp) {
         if (DIAG && !need64) member_stats_add(bp, mi, m, acc, false);
       }
     }
-    unsigned todo = __ballot_sync(0xffffffffu, need64);
-    if (__popc(todo) > 16) {
-      // many FP64 nodes in this warp's round (the first steps of new
-      // members): one per lane costs less FP64 issue than one per warp
-      if (need64) {
-        const int mi = (int)(e >> 32);
-        const unsigned node = (unsigned)(e & 0xffffffffu) & ~kTagRefine;
-        const MemberDesc& m = bp.members[mi];
-        const float* in = pick(m, m.parity0 + bp.step);
-        float* out = pick(m, m.parity0 + bp.step + 1);
-        StepParams g;   // geometry for src_index
-        g.nx = m.nx;
-        g.ny = m.ny;
-        g.nz = m.nz;
-        int x, y, z;
-        coords(m, node, x, y, z);
-        Acc acc;
-        acc.init();
-        const StepParams pp = params(m);
-        auto run = [&](auto lat) {
-          using L = decltype(lat);
-          Node64<L> nd;
-#pragma unroll
-          for (int i = 0; i < L::Q; ++i)
-            nd.f[i] = L::w(i) * m.rho0 +
-                      (double)in[(size_t)i * m.n + src_index<L>(g, i, x, y, z)];
-          auto store = [&](int i, double val) {
-            if (i < 0)
-              m.alpha_map[node] = (float)val;
-            else
-              out[(size_t)i * m.n + node] = (float)(val - L::w(i) * m.rho0);
-          };
-          collide64<L, MODE_FORMULA, 0>(nd, pp, true, acc, DIAG != 0, store);
-        };
-        if (m.lattice == 1)
-          run(D3Q27{});
-        else
-          run(D2Q9{});
-        if (DIAG) member_stats_add(bp, mi, m, acc, true);
+    // FP64 nodes of this round, as in k_far_fixup: one per warp for a few,
+    // one per lane for many; a queue longer than the grid (new members'
+    // first steps) collects them per warp and runs them 32 at a time
+    const unsigned todo = __ballot_sync(0xffffffffu, need64);
+    if (!bulk && __popc(todo) > 16) {
+      if (need64) fp64_lane(e);
+    } else if (bulk) {
+      const int nk = __popc(todo);
+      if (npend + nk > 32) flush();
+      if (need64) pend[npend + __popc(todo & ((1u << lane) - 1u))] = e;
+      npend += nk;
+    } else {
+      unsigned m = todo;
+      while (m) {
+        const int src_lane = __ffs(m) - 1;
+        m &= m - 1;
+        fp64_warp(__shfl_sync(0xffffffffu, e, src_lane));
       }
-      todo = 0u;
     }
-    while (todo) {
-      const int src_lane = __ffs(todo) - 1;
-      todo &= todo - 1;
-      const unsigned long long ee = __shfl_sync(0xffffffffu, e, src_lane);
-      const int mi = (int)(ee >> 32);
-      const unsigned node = (unsigned)(ee & 0xffffffffu) & ~kTagRefine;
-      const MemberDesc& m = bp.members[mi];
-      const float* in = pick(m, m.parity0 + bp.step);
-      float* out = pick(m, m.parity0 + bp.step + 1);
-      int x, y, z;
-      coords(m, node, x, y, z);
-      auto run = [&](auto lat, const LanePop& lp) {
-        using L = decltype(lat);
-        double f = 0.0;
-        if (lp.on) {
-          int xs = x - lp.c[0], ys = y - lp.c[1], zs = z - lp.c[2];
-          xs = xs < 0 ? xs + m.nx : (xs >= m.nx ? xs - m.nx : xs);
-          ys = ys < 0 ? ys + m.ny : (ys >= m.ny ? ys - m.ny : ys);
-          zs = zs < 0 ? zs + m.nz : (zs >= m.nz ? zs - m.nz : zs);
-          const size_t src =
-              ((size_t)zs * (size_t)m.ny + (size_t)ys) * (size_t)m.nx +
-              (size_t)xs;
-          f = lp.w * m.rho0 + (double)in[(size_t)lane * m.n + src];
-        }
-        return formula64_warp<L>(lp, f, m.beta64, [&](double val) {
-          out[(size_t)lane * m.n + node] = (float)(val - lp.w * m.rho0);
-        });
-      };
-      const Warp64 r = m.lattice == 1 ? run(D3Q27{}, lp27) : run(D2Q9{}, lp9);
-      if (lane == 0) {
-        if (r.flags & (NF_BAD_NEG | NF_BAD_NONFINITE)) {
-          atomicOr(bp.err_flags, r.flags);
-        } else {
-          if (m.alpha_map) m.alpha_map[node] = (float)r.alpha;
-          if (DIAG) {
-            Acc acc;
-            acc.init();
-            acc.add_moments(r.rho - m.rho0, r.j, r.rho);
-            acc.add_alpha(r.alpha, r.flags, 0);
-            member_stats_add(bp, mi, m, acc, true);
-          }
-        }
-      }
+  }
+  if (npend > 0) {   // bulk remainder: few nodes run one per warp
+    __syncwarp();
+    if (npend > 5) {
+      flush();
+    } else {
+      for (int j = 0; j < npend; ++j) fp64_warp(pend[j]);
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) bp.far_count[(bp.step & 1) ^ 1] = 0u;
