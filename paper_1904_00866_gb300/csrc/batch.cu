@@ -107,10 +107,14 @@ cudaError_t launch_batch(int tb, int diag, const BatchParams& bp, int grid,
 cudaError_t launch_batch_refine(int diag, const BatchParams& bp, int blocks,
                                 cudaStream_t s) {
   if (blocks > kMaxRefineBlocks) return cudaErrorInvalidValue;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = 2 * sms;   // two 128-register blocks per SM
   if (diag)
-    k_batch_refine<1><<<152, 256, 0, s>>>(bp, blocks);
+    k_batch_refine<1><<<grid, 256, 0, s>>>(bp, blocks);
   else
-    k_batch_refine<0><<<152, 256, 0, s>>>(bp, blocks);
+    k_batch_refine<0><<<grid, 256, 0, s>>>(bp, blocks);
   count_launch();
   return cudaGetLastError();
 }

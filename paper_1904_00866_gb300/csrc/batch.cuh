@@ -324,11 +324,12 @@ __device__ __forceinline__ void member_stats_add(const BatchParams& bp, int mi,
 }
 
 // Second stage of the undecided nodes the batch kernel (`blocks` blocks)
-// buffered; a node it leaves undecided joins the deferred-node queue for
-// the FP64 fixup that follows.
+// buffered, two blocks per SM; a node it leaves undecided joins the
+// deferred-node queue for the fixup that follows (tagged when the
+// double-float series pass may still decide it).
 template <int DIAG>
-__global__ void __launch_bounds__(256) k_batch_refine(const BatchParams bp,
-                                                      int blocks) {
+__global__ void __launch_bounds__(256, 2) k_batch_refine(const BatchParams bp,
+                                                         int blocks) {
   __shared__ unsigned pre[kMaxRefineBlocks + 1];
   block_prefix(bp.refine_counts, blocks, pre);
   const unsigned total = pre[blocks];
@@ -374,19 +375,17 @@ __global__ void __launch_bounds__(256) k_batch_refine(const BatchParams bp,
       }
       float (&vq)[L::Q] = *reinterpret_cast<float (*)[L::Q]>(v);
       auto out32 = [&](int i, float val) { out[(size_t)i * m.n + node] = val; };
-      // the double-float series pass for nodes the FP32 series leaves open
-      int st = refine_deferred<L, true, DIAG, 0, false>(pp, vq, node, ap, acc,
-                                                        out32);
-      if (st == kStageRetry)
-        st = refine_deferred<L, true, DIAG, 0, true>(pp, vq, node, ap, acc,
-                                                     out32);
-      return st == kStageDone;
+      return refine_deferred<L, true, DIAG, 0, false>(pp, vq, node, ap, acc,
+                                                      out32);
     };
-    const bool done = m.lattice == 1 ? run(D3Q27{}) : run(D2Q9{});
-    if (!done) {
+    const int st = m.lattice == 1 ? run(D3Q27{}) : run(D2Q9{});
+    if (st != kStageDone) {
+      // kStageRetry: tagged, so that the fixup (whose register budget
+      // holds it) runs the double-float series pass before any FP64
       const unsigned q = atomicAdd(&bp.far_count[bp.step & 1], 1u);
       if (q < bp.far_cap)
-        bp.far_queue[q] = ((unsigned long long)mi << 32) | node;
+        bp.far_queue[q] = ((unsigned long long)mi << 32) |
+                          (node | (st == kStageRetry ? kTagRefine : 0u));
       else
         atomicOr(bp.err_flags, NF_BAD_NONFINITE);   // cannot happen
     } else if (DIAG) {
