@@ -101,13 +101,19 @@ typedef enum {
  * bound).
  *   ELBM_DECISION_EXACT (default): a second stage recomputes f^eq - f in
  *     double-float arithmetic and retakes the acceptance test after Eq. (8)
- *     and Eq. (9) with that error bound (FP64 for the rare node still
+ *     and Eq. (9) with that error bound (then with the leading terms of
+ *     Delta H(2) in double-float as well, and FP64 for the rare node still
  *     undecided), so every node takes the branch the exact arithmetic
- *     takes: alpha and the Fig. 5 counter are the paper's.
+ *     takes and an Eq. (9) alpha lies within 2^-16 of the chord of the
+ *     stored state: alpha and the Fig. 5 counter are the paper's.  Costs
+ *     about 10 % per step on developed 3D flows, more where most nodes are
+ *     within FP32 noise of equilibrium (the first step after
+ *     elbm_init_fields; thin shear layers).
  *   ELBM_DECISION_CERTIFIED: such a node keeps the certified alpha -- the
- *     Eq. (9) chord on the upper bounds, rounded down, or 1 -- which also
- *     satisfies H(f*(alpha)) <= H(f) and is within about 1e-5 of the exact
- *     alpha; faster (no second stage).
+ *     Eq. (9) chord on the upper bounds, rounded down, or 1 when no chord
+ *     is certified -- which also satisfies H(f*(alpha)) <= H(f) but may
+ *     take the other branch than the exact arithmetic; faster (no second
+ *     stage).
  * FP64 storage and the ROOT / SECANT modes are unaffected. */
 typedef enum {
   ELBM_DECISION_EXACT = 0,
@@ -143,7 +149,8 @@ typedef struct {
                                decided by the double-float second stage   */
   long long n_far;          /* FP32 FORMULA: node solved in FP64 (far from
                                equilibrium, invalid, or undecided by the
-                               second stage)                              */
+                               second stage and its double-float series
+                               pass)                                      */
   long long n_degenerate;   /* f^eq == f: alpha = 2                       */
   long long n_root_iters;   /* ROOT/SECANT iterations                     */
   long long n_root_cap;     /* ROOT stopped at the iteration cap          */

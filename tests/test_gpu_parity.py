@@ -310,6 +310,35 @@ def test_fp64_fixup_of_far_nodes_vs_oracle(elbm, orc, lat, shape, init,
     assert np.all(np.abs(fg - o.f) <= tol), np.max(np.abs(fg - o.f) / tol)
 
 
+@pytest.mark.parametrize("dtype", ["fp32_shifted", "fp16_shifted"])
+def test_fixup_bulk_path_matches_per_lane_path(elbm, dtype):
+    """The first step after initialisation leaves nearly every node
+    undecided in FP32 (n is pure rounding noise), so the fixup's queue is
+    longer than its grid: each warp collects its FP64 nodes and runs them
+    32 at a time, one per lane.  The same step with the FP64 check runs
+    every FP64 node on its own lane directly; the per-node arithmetic is
+    the same, so populations and alpha maps agree bit for bit.  The checked
+    step also takes the FP64 branch at every non-degenerate node."""
+    n = 64
+    rho, u = W.taylor_green_3d(n, 0.05)
+    res = []
+    for check in (1, 0):
+        g = elbm.Lattice("D3Q27", n, n, n, nu=1e-3, dtype=dtype)
+        g.init_fields(rho, u)
+        g.set_diagnostics(diag_every=check, check_every=check,
+                          alpha_map_every=1)
+        g.step(1, "formula")
+        if check:
+            s = g.entropy_stats()
+            assert s["n_violations"] == 0
+            assert s["n_decision_mismatch"] == 0
+            assert s["n_band"] + s["n_far"] > 0.9 * n ** 3   # bulk regime
+        res.append((g.populations(), g.alpha_map()))
+        g.close()
+    assert np.array_equal(res[0][0], res[1][0])
+    assert np.array_equal(res[0][1], res[1][1])
+
+
 def test_fp32_random_phase_zero_violations(elbm):
     n = 32
     rho, u = W.random_phase_3d(n, seed=2, umax=0.05)
