@@ -8,8 +8,10 @@
 // alpha_formula64: ~2,400 FP64 instructions for D3Q27, most of them the 27
 // divisions and logarithms) therefore holds its warp for ~75 us, and a
 // fixup with a few thousand such nodes ends ~0.2 ms after its last node
-// started, however they are spread.  Per lane the same node takes ~150
-// FP64 instructions.
+// started, however they are spread.  Spread over the lanes the node takes
+// ~460 FP64 warp instructions (divisions, logarithms and the reductions)
+// and so ends ~6x sooner; in bulk, one node per lane costs fewer FP64
+// instructions per node (~75), which the fixups use on long queues.
 //
 // The arithmetic is that of node64_prepare and alpha_formula64 (Eq. (8),
 // the acceptance test after it, Eq. (9)), population by population; only

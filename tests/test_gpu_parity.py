@@ -312,14 +312,17 @@ def test_fp64_fixup_of_far_nodes_vs_oracle(elbm, orc, lat, shape, init,
 
 @pytest.mark.parametrize("dtype", ["fp32_shifted", "fp16_shifted"])
 def test_fixup_bulk_path_matches_per_lane_path(elbm, dtype):
-    """The first step after initialisation leaves nearly every node
-    undecided in FP32 (n is pure rounding noise), so the fixup's queue is
-    longer than its grid: each warp collects its FP64 nodes and runs them
-    32 at a time, one per lane.  The same step with the FP64 check runs
-    every FP64 node on its own lane directly; the per-node arithmetic is
-    the same, so populations and alpha maps agree bit for bit.  The checked
-    step also takes the FP64 branch at every non-degenerate node."""
-    n = 64
+    """The first step after initialisation leaves most nodes undecided in
+    FP32 (n is rounding noise), so the fixup's queue is longer than its
+    grid: each warp collects its FP64 nodes and runs them 32 at a time, one
+    per lane (the last few of a warp, one per warp).  The same step with
+    the FP64 check runs every FP64 node on its own lane directly.  The
+    per-node arithmetic is the same except for the order of the sums in
+    the one-per-warp remainder, so populations agree to the FP32 rounding
+    of the relaxation and alpha maps to one FP32 rounding (2^-22
+    relative).  The checked step also takes the FP64 branch at every
+    non-degenerate node."""
+    n = 96
     rho, u = W.taylor_green_3d(n, 0.05)
     res = []
     for check in (1, 0):
@@ -332,11 +335,14 @@ def test_fixup_bulk_path_matches_per_lane_path(elbm, dtype):
             s = g.entropy_stats()
             assert s["n_violations"] == 0
             assert s["n_decision_mismatch"] == 0
-            assert s["n_band"] + s["n_far"] > 0.9 * n ** 3   # bulk regime
-        res.append((g.populations(), g.alpha_map()))
+            # a fixup queue longer than its grid (304 x 256 threads)
+            assert s["n_band"] + s["n_far"] > 77824
+        res.append((g.populations(), g.alpha_map().astype(np.float64)))
         g.close()
-    assert np.array_equal(res[0][0], res[1][0])
-    assert np.array_equal(res[0][1], res[1][1])
+    (f0, a0), (f1, a1) = res
+    assert np.all(np.abs(f0 - f1) <= 2e-7 * np.abs(f0))
+    assert np.all(np.abs(a0 - a1) <= 2.0 ** -22 * a0)
+    assert np.mean(a0 == a1) > 0.999
 
 
 def test_fp32_random_phase_zero_violations(elbm):
