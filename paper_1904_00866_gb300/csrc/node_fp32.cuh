@@ -215,7 +215,14 @@ __device__ __forceinline__ DH32 series_dh32(const float (&M)[9], bool k8,
     rnd = 0.0f;
   }
   const float M2 = M[2];
-  h.e2 = M2 * (2.02f * Ex +
+  // First-order propagation of the x errors: with x_i^c = x_i + dx_i
+  // (|dx_i| <= Ex) and n_i^c = f_i (dx_i - x_i e_i) + n_i (e_i the
+  // quotient's relative rounding, below 3u), the computed term
+  // n^c (x^c)^(k-1) is off by k f x^(k-1) dx - f x^k e, so Delta H(2) is off
+  // by at most sum_k |c_k(2)| k f |x|^(k-1) Ex + 3u sum_k |c_k(2)| f |x|^k
+  // <= M2 Ex (1 + 2.67 xabs + 5.5 xabs^2 + ...) + 2u xabs M2, and
+  // 1 + 4 xabs covers the bracket for xabs <= 1/8 (1.445 there).
+  h.e2 = M2 * (1.01f * (1.0f + 4.0f * xabs) * Ex + 2.0f * uu * xabs +
                gq * xabs * (0.34f + xabs * (0.7f + xabs * (1.2f + 1.8f * xabs))) +
                tr2) +
          4.0f * uu * (fabsf(M[3]) * (1.0f / 3.0f) + fabsf(M[4]) * (2.0f / 3.0f) +

@@ -342,7 +342,6 @@ def test_fixup_bulk_path_matches_per_lane_path(elbm, dtype):
     (f0, a0), (f1, a1) = res
     assert np.all(np.abs(f0 - f1) <= 2e-7 * np.abs(f0))
     assert np.all(np.abs(a0 - a1) <= 2.0 ** -22 * a0)
-    assert np.mean(a0 == a1) > 0.999
 
 
 def test_fp32_random_phase_zero_violations(elbm):
