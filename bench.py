@@ -54,7 +54,7 @@ FALLBACK_HBM_GBS = 6800.0
 # dram__bytes_read.sum + dram__bytes_write.sum per launch / nodes), valid
 # while the kernel sources hash to `sha`; scaled to the workload by node
 # count (traffic grows in proportion).
-TRAFFIC_RECORD = {"sha": "8179d3df7bf1fa8b", "bytes_per_node": 222.5637,
+TRAFFIC_RECORD = {"sha": "264ee1a06d018153", "bytes_per_node": 219.1171,
                   "files": ['df32.cuh', 'fp16_storage.cuh', 'lattice.cuh',
                             'node_fp32.cuh', 'node_fp64.cuh', 'sc32.cuh',
                             'stats.cuh', 'stream_collide.cuh']}
