@@ -211,9 +211,12 @@ ELBM_API elbm_status elbm_set_decision(elbm_handle *h, elbm_decision decision);
 /* f^0 = f^eq(rho, u) at every node.  rho: [nz][ny][nx] > 0,
  * u: [d][nz][ny][nx] with |u_a| < 1, FP64 host buffers.  Resets the step
  * counter to 0 and sets rho0 to the FP32-rounded mean of rho.
- * The first call of elbm_init_fields, elbm_moments or elbm_enstrophy
- * allocates a device staging buffer of (1 + d) x n doubles, which the
- * handle keeps (and reuses) until elbm_destroy. */
+ * Page-locked host buffers (cudaHostAlloc, cudaHostRegister, pinned
+ * framework tensors) are read by the init kernels directly over the host
+ * link; pageable ones go through a device staging buffer of (1 + d) x n
+ * doubles, allocated by the first such call of elbm_init_fields,
+ * elbm_moments or elbm_enstrophy and kept (and reused) until
+ * elbm_destroy.  Synchronises. */
 ELBM_API elbm_status elbm_init_fields(elbm_handle *h, const double *rho,
                              const double *u);
 /* Same with device pointers (on the handle's device, FP64). */
@@ -236,7 +239,7 @@ ELBM_API elbm_status elbm_set_populations(elbm_handle *h, const double *f);
  * decided again with that smaller error; the rare node still undecided is
  * solved in FP64.  So each node takes the branch of the exact arithmetic
  * and H(f*(alpha)) <= H(f) holds for the stored state.  Nodes with
- * max|x_i| > 1/8, |u_a| >= 1/2 or invalid populations are solved in FP64.
+ * max|x_i| > 1/8, |u_a| >= 1/4 or invalid populations are solved in FP64.
  * FP32 and FP16 storages take fewer than 2^31 nodes. */
 ELBM_API elbm_status elbm_step(elbm_handle *h, long long nsteps, elbm_alpha_mode mode);
 
@@ -246,7 +249,9 @@ ELBM_API elbm_status elbm_sync(elbm_handle *h);
 /* Density [nz][ny][nx] and velocity [d][nz][ny][nx] of f^n (host, FP64):
  * rho = sum_i f_i and rho u = sum_i c_i f_i, the mass and momentum moments
  * that the equilibrium of Eq. (3) conserves (the constraints stated after
- * Eq. (3)).  Either pointer may be NULL.  Synchronises. */
+ * Eq. (3)).  Either pointer may be NULL.  When both are page-locked host
+ * buffers the kernel writes them directly; otherwise through the staging
+ * buffer (elbm_init_fields).  Synchronises. */
 ELBM_API elbm_status elbm_moments(elbm_handle *h, double *rho_out, double *u_out);
 
 /* Populations f^n as FP64 [Q][nz][ny][nx] (host).  Synchronises. */

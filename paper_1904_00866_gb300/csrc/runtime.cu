@@ -469,11 +469,31 @@ static elbm_status init_common(elbm_handle* h, const double* rho_dev,
   return st;
 }
 
+// The device-side address of a host buffer the GPU can access directly
+// (page-locked host memory, e.g. cudaHostAlloc or a pinned framework
+// tensor), else null.  Kernels then read or write it over the host link
+// themselves, with no staging copy in device memory.
+static void* host_view(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();   // clear the error state of the query
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 elbm_status elbm_init_fields(elbm_handle* h, const double* rho,
                              const double* u) {
   if (!h || !rho || !u) return h ? fail(h, ELBM_EINVAL, "NULL field") : ELBM_EINVAL;
   elbm_status st = ensure_buffers(h);
   if (st) return st;
+  const double* rho_v = (const double*)host_view(rho);
+  const double* u_v = (const double*)host_view(u);
+  if (rho_v && u_v) {   // page-locked: the init kernels read them directly
+    st = init_common(h, rho_v, u_v);
+    cudaStreamSynchronize(h->stream);
+    return st;
+  }
   double* tmp = fields_staging(h);
   if (!tmp) return fail(h, ELBM_ENOMEM, "staging allocation failed");
   cudaError_t e = cudaMemcpyAsync(tmp, rho, sizeof(double) * h->n,
@@ -699,9 +719,17 @@ elbm_status elbm_moments(elbm_handle* h, double* rho_out, double* u_out) {
   if (!h->allocated) return fail(h, ELBM_ESTATE, "fields not initialised");
   elbm_status st = check_errors(h);
   if (st) return st;
+  Geo g = geo(h);
+  double* rho_v = rho_out ? (double*)host_view(rho_out) : nullptr;
+  double* u_v = u_out ? (double*)host_view(u_out) : nullptr;
+  if (rho_v && u_v) {   // page-locked: the kernel writes them directly
+    DISPATCH_LT(h, k_moments, g, h->f[h->cur], rho_v, u_v);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "moments");
+    return ELBM_OK;
+  }
   double* tmp = fields_staging(h);
   if (!tmp) return fail(h, ELBM_ENOMEM, "staging allocation failed");
-  Geo g = geo(h);
   DISPATCH_LT(h, k_moments, g, h->f[h->cur], tmp, tmp + h->n);
   cudaError_t e = cudaSuccess;
   if (rho_out)
