@@ -53,11 +53,12 @@ class Server:
 
     batch: object with the Batch interface; fields: callable
     (lattice, n, seed) -> (rho, u); budget_bytes: device memory the resident
-    runs may use; max_members: resident runs at most; burst: steps per
+    runs may use; max_members: resident runs at most (the batch's member
+    limit, 256, by default); burst: steps per
     burst; clock: seconds (monotonic); keep_results: store final fields.
     """
 
-    def __init__(self, batch, fields, budget_bytes=150e9, max_members=64,
+    def __init__(self, batch, fields, budget_bytes=150e9, max_members=256,
                  burst=16, clock=time.monotonic, sleep=time.sleep,
                  keep_results=True):
         self.batch = batch
