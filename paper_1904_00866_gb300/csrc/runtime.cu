@@ -232,12 +232,18 @@ static elbm_status ensure_buffers(elbm_handle* h) {
     // most nodes of a flow whose non-equilibrium part is near FP32
     // resolution (a thin shear layer at Re 30,000) and of the first step
     // after initialisation; a full buffer sends the rest to the gathering
-    // queue.  D2Q9: every node (48-byte records); D3Q27: n / 16 entries
-    // (8 B per node), at least 65,536.
+    // queue, where each node costs ~3x more (gather, FP32 stage again).
+    // D2Q9: every node (48-byte records); D3Q27: half the nodes, at most
+    // 2^26 records (8.6 GB) unless n / 16 is more, at least 65,536.
     const long long cap =
-        h->q == 9 ? h->n
-                  : std::min<long long>(h->n,
-                                        std::max<long long>(h->n / 16, 65536));
+        h->q == 9
+            ? h->n
+            : std::min<long long>(
+                  h->n, std::max<long long>(
+                            65536, std::min<long long>(
+                                       h->n / 2,
+                                       std::max<long long>(h->n / 16,
+                                                           1LL << 26))));
     const int rec = h->q == 27 ? refine_record<D3Q27>() : refine_record<D2Q9>();
     h->refine_buf =
         (float*)dev_alloc(h, sizeof(float) * (size_t)rec * (size_t)cap);
